@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the WENO5-CT MHD step (libw5ct) on one GB300.
+
+Workload (default): 256^3 periodic box, uniform rho = 1, beta = 1 mean field
+along x, solenoidal Gaussian random-phase velocity with a k^-5/3 spectrum
+for 2 <= |k| <= 32 at rms Mach 1 (seed 1812), divergence-free field
+perturbation of 10% rms from an edge vector potential (seed 1813); WENO-Z,
+CFL 0.8, dt from the device CFL reduction every step.  The state (>= 4 GB)
+is far larger than L2, so no L2 flush is needed between steps.
+
+One JSON line: `value` = FP64 zone-updates/s (the paper's 8-byte
+arithmetic); `fp32_bulk` = the FP32-bulk form (float flux arithmetic,
+double accumulation) with its L1 error against the FP64 run after the same
+steps at the same dt sequence.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference] [--n 256]
+
+With N > 1 (torchrun) every rank advances its own independent replica
+("replicas only": the path has no data exchange) and the slowest rank's time
+is used.  --impl reference times the CPU oracle on the host cores on a
+bounded 64^3 sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic flop count per interface of one sweep (the paper's steps as
+# the oracle performs them: interface average, Appendix A eigensystem,
+# 6-point projection of F and q onto 7 fields, LF split and two phi_N per
+# field, back-projection, CT transport fluxes) and per cell of one sweep
+# (primitives, flux, three speeds).  Divisions and square roots count 1.
+FACE_FLOPS = 2720
+CELL_FLOPS = 60
+SWEEP_FLOPS_PER_ZONE = FACE_FLOPS + CELL_FLOPS
+# Peaks: FP32 from the unit counts (152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz);
+# FP64 from the published GB300 rate (1.25 TFLOP/s); measured copy bandwidth.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(n):
+    return {
+        "workload": f"periodic {n}^3 MHD turbulence: rho=1, beta=1 mean B along x, k^-5/3 solenoidal velocity "
+                    f"2<=|k|<=32 at rms Mach 1 (seed 1812), 10% rms div-free dB (seed 1813); WENO-Z, CFL 0.8, "
+                    f"gamma 5/3, dt from the CFL reduction each step",
+        "zones": n ** 3,
+        "grid": [n, n, n],
+        "l2_policy": "state larger than L2 (>= 4 GB), no flush",
+        "parallelism": "replicas",
+    }
+
+
+def make_ic(n):
+    from paper_1812_04278_gb300 import inputs
+    return inputs.turbulent_state(n, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1, kmin=2, kmax=32)
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_sweep32.cu", "w5ct_sweep64.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1812_04278_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# DRAM traffic of one sweep launch per zone, from an ncu capture of the
+# kernel whose source hash is given (None until captured).
+SWEEP_TRAFFIC = {"fp64": None, "fp32": None}
+
+
+def l1_error(a_cons, a_b, b_cons, b_b):
+    """Geometric L1 norm over the state components (Sec. 4 of the paper)."""
+    n = a_cons[0].size
+    comps = [np.abs(a_cons[f] - b_cons[f]).sum() / n for f in range(5)] + \
+            [np.abs(a_b[f] - b_b[f]).sum() / n for f in range(3)]
+    return float(np.sqrt(np.sum(np.square(comps))))
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    import oracle
+    from paper_1812_04278_gb300 import inputs
+    oracle.build()
+    ns = 64
+    cons, bface = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
+                                         kmin=2, kmax=min(32, ns // 2 - 1))
+    o = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
+    o.set_state(cons, bface)
+    for _ in range(args.warmup):
+        o.step(o.cfl_dt())
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(o.cfl_dt())
+    el = time.perf_counter() - t0
+    value = ns ** 3 * args.steps / el
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value,
+        "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps * (args.n / ns) ** 3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.n),
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{ns}^3 box of the same turbulence generator, {args.steps} full steps"},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ native arm
+
+
+def timed_run(torch, w5, shape, dx, cons_d, bface_d, precision, steps, warmup, dt_log=None, sampler=None,
+              barrier=None):
+    stream = torch.cuda.current_stream()
+    s = w5.Solver(shape, dx, w5.make_config(precision=precision, weno_variant=w5.W5CT_WENO_Z),
+                  stream=stream.cuda_stream)
+    s.set_state(cons_d, bface_d)
+    for k in range(warmup):
+        s.step_cfl(None if dt_log is None else dt_log[k:k + 1])
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    launches0 = w5.w5ct_launch_count(s.ctx)
+    w5.w5ct_set_timing(s.ctx, True)
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(steps):
+        s.step_cfl(None if dt_log is None else dt_log[warmup + k:warmup + k + 1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    nsweep, sweep_ms = w5.w5ct_sweep_timing(s.ctx)
+    w5.w5ct_set_timing(s.ctx, False)
+    launches = w5.w5ct_launch_count(s.ctx) - launches0
+    return s, ms, nsweep, sweep_ms, launches, clocks
+
+
+def run_native(args):
+    import torch
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_1812_04278_gb300 import build
+    build.build()
+    from paper_1812_04278_gb300 import w5ct as w5
+
+    n = args.n
+    shape = (n, n, n)
+    dx = (1.0 / n,) * 3
+    zones = n ** 3
+    cons, bface = make_ic(n)
+    cons_d = torch.from_numpy(cons).cuda()
+    bface_d = torch.from_numpy(bface).cuda()
+    barrier = (lambda: dist.barrier()) if dist is not None else None
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- FP64 (headline)
+    nlog = args.warmup + args.steps
+    dt_log = torch.zeros(nlog, dtype=torch.float64, device="cuda")
+    sampler = ClockSampler(local) if rank == 0 else None
+    s64, ms64, nsw64, swms64, launches64, clocks = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP64,
+                                                             args.steps, args.warmup, dt_log, sampler, barrier)
+    ms64 = max_over_ranks(ms64)
+    c64 = torch.empty_like(cons_d)
+    b64 = torch.empty_like(bface_d)
+    w5.w5ct_get_state(s64.ctx, c64, b64, None, 1)
+    divb64 = s64.div_b_norm()[0]
+    s64.close()
+
+    # ---- FP32-bulk
+    s32, ms32, nsw32, swms32, launches32, _ = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP32_BULK,
+                                                        args.steps, args.warmup, None, None, barrier)
+    ms32 = max_over_ranks(ms32)
+    # error pass: same IC and the FP64 run's dt sequence
+    s32.set_state(cons_d, bface_d)
+    for k in range(nlog):
+        w5.w5ct_step_dev(s32.ctx, dt_log[k:k + 1])
+    c32 = torch.empty_like(cons_d)
+    b32 = torch.empty_like(bface_d)
+    w5.w5ct_get_state(s32.ctx, c32, b32, None, 1)
+    divb32 = s32.div_b_norm()[0]
+    s32.close()
+    c64h, b64h, c32h, b32h = (t.cpu().numpy() for t in (c64, b64, c32, b32))
+    l1 = l1_error(c32h, b32h, c64h, b64h)
+    l1_ref = l1_error(c64h, b64h, cons, bface)     # how far the FP64 state moved
+    relmax = float(max(np.abs(c32h - c64h).max(), np.abs(b32h - b64h).max()) /
+                   max(np.abs(c64h).max(), np.abs(b64h).max()))
+    del c64, b64, c32, b32
+
+    # ---- end to end through the C ABI with host buffers (FP64)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    hc = torch.from_numpy(cons).pin_memory()
+    hb = torch.from_numpy(bface).pin_memory()
+    oc = torch.empty_like(hc).pin_memory()
+    ob = torch.empty_like(hb).pin_memory()
+    se = w5.Solver(shape, dx, w5.make_config(precision=w5.W5CT_FP64), stream=torch.cuda.current_stream().cuda_stream)
+    w5.w5ct_set_state(se.ctx, hc.data_ptr(), hb.data_ptr(), 0)
+    se.step_cfl()
+    w5.w5ct_get_state(se.ctx, oc.data_ptr(), ob.data_ptr(), None, 0)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        w5.w5ct_set_state(se.ctx, hc.data_ptr(), hb.data_ptr(), 0)
+        se.step_cfl()
+        w5.w5ct_get_state(se.ctx, oc.data_ptr(), ob.data_ptr(), None, 0)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    se.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks = load_peaks()
+    value64 = world * zones * args.steps / (ms64 * 1e-3)
+    value32 = world * zones * args.steps / (ms32 * 1e-3)
+    sweep_flops = SWEEP_FLOPS_PER_ZONE * zones
+    ach64 = sweep_flops / (swms64 / nsw64 * 1e-3) / 1e12
+    ach32 = sweep_flops / (swms32 / nsw32 * 1e-3) / 1e12
+    line = {
+        "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)",
+        "value": value64,
+        "unit": "zone-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms64 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(n),
+        "roofline": {"kernel": "sweep_kernel (FP64)", "bound": "alu", "achieved": ach64, "peak": PEAK_FP64_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
+                     "traffic": SWEEP_TRAFFIC["fp64"], "launch_ms": swms64 / nsw64,
+                     "algorithmic_flops_per_launch": sweep_flops,
+                     "peak_source": "published GB300 FP64 rate 1.25 TFLOP/s (probe measured 1.0 TFLOP/s DFMA)"},
+        "fp32_bulk": {
+            "value": value32, "unit": "zone-updates/s", "ms_per_step": ms32 / args.steps, "dtype": "f32",
+            "accumulate": "f64", "speedup_vs_fp64": value32 / value64,
+            "l1_vs_fp64": l1, "l1_fp64_change": l1_ref, "max_rel_vs_fp64": relmax, "div_b_linf": divb32,
+            "error_steps": nlog,
+            "roofline": {"kernel": "sweep_kernel (FP32)", "bound": "alu", "achieved": ach32,
+                         "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
+                         "traffic": SWEEP_TRAFFIC["fp32"], "launch_ms": swms32 / nsw32,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "gpu_launches": launches32,
+        },
+        "div_b_linf": divb64,
+        "e2e": {"value": world * zones * e2e_steps / e2e_s, "unit": "zone-updates/s",
+                "h2d_bytes_per_step": int(cons.nbytes + bface.nbytes),
+                "d2h_bytes_per_step": int(cons.nbytes + bface.nbytes), "steps": e2e_steps},
+        "gpu_launches": launches64,
+        "clocks": clocks,
+        "kernel_src": kernel_source_hash(),
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args):
+    """The oracle, as it stands, on the host cores: full steps on a 64^3
+    sample of the same workload until about args.cpu_seconds have passed."""
+    import oracle
+    from paper_1812_04278_gb300 import inputs
+    oracle.build()
+    ns = 64
+    cons, bface = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
+                                         kmin=2, kmax=min(32, ns // 2 - 1))
+    o = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
+    o.set_state(cons, bface)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(o.cfl_dt())
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= args.cpu_seconds:
+            break
+    return {"value": ns ** 3 * steps / el, "unit": "zone-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{steps} full steps of a {ns}^3 box of the same turbulence generator",
+            "seconds": el}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * w5ct.h -- C ABI of libw5ct, a GB300 (sm_103a) implementation of the
+ * fifth-order finite-difference WENO + constrained-transport ideal-MHD
+ * scheme of Donnert et al., "WENO-Wombat" (arXiv:1812.04278).
+ *
+ * One context advances one periodic patch with the paper's scheme:
+ *   - the per-axis characteristic flux update (Sec. 2.2, Eq. FWENO, with
+ *     the eigenvectors of Appendix A and local Lax-Friedrichs splitting),
+ *   - the Ryu et al. transport-flux CT update of the face fields
+ *     (Sec. 2.3, Eqs. fct1-fct6, ox1-ox3),
+ *   - the classical four-stage RK4 (Sec. 2.1) interleaved with CT
+ *     (Sec. 3.1.3), and the CFL time step (Sec. 2.1, Eq. cfl).
+ *
+ * Conventions shared by every call
+ *   Grid: periodic, nx*ny*nz cells, x fastest: cell (i,j,k) has linear
+ *     index i + nx*(j + ny*k).  Cell spacings dx, dy, dz.
+ *   Conserved cell state "cons": 5 planes of nx*ny*nz doubles, in the order
+ *     rho, m_x, m_y, m_z, E (E = total energy, Eq. P).
+ *   Face field "bface": 3 planes: b_x at the face (i+1/2, j, k), b_y at
+ *     (i, j+1/2, k), b_z at (i, j, k+1/2), each stored at the index of
+ *     cell (i, j, k) (the forward face, Sec. 2.3).
+ *   Cell field "bcell": 3 planes of the fourth-order face-to-centre
+ *     interpolation of bface (Sec. 2.3).
+ *   Pointers marked "host or device" are read or written only during the
+ *     call; when on_device != 0 they must be device pointers of the current
+ *     device, else host pointers.  The library never keeps a caller pointer.
+ *   Ownership: the context owns every device buffer it allocates
+ *     (cudaMalloc at w5ct_init_grid, cudaFree at w5ct_destroy / re-init).
+ *   Streams: all device work is enqueued on the stream given in the
+ *     config (a cudaStream_t, NULL = legacy default stream).  Calls that
+ *     return values to the host synchronise that stream; w5ct_step* do not.
+ *   Errors: every call returns 0 (W5CT_OK) or a negative code below; the
+ *     text of the last error is available from w5ct_last_error.  No call
+ *     throws, traps or aborts.  A state that becomes non-physical inside a
+ *     step (rho <= 0, P <= 0 or NaN after the optional floors) raises a
+ *     device flag that the next synchronising call reports as
+ *     W5CT_ERR_NONPHYSICAL.
+ */
+#ifndef W5CT_H
+#define W5CT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define W5CT_OK 0
+#define W5CT_ERR_ARG (-1)          /* invalid argument (null pointer, bad size, dt <= 0, ...) */
+#define W5CT_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define W5CT_ERR_STATE (-3)        /* call out of order (e.g. step before set_state) */
+#define W5CT_ERR_NONPHYSICAL (-4)  /* rho <= 0, P <= 0 or NaN met inside the scheme */
+#define W5CT_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
+
+#define W5CT_WENO_JS 0             /* Jiang-Shu weights, eps = 1e-6 (Sec. 2.2) */
+#define W5CT_WENO_Z 1              /* WENO-Z weights (Sec. 2.2), ratio squared */
+
+#define W5CT_FP64 0                /* every operation in IEEE double */
+#define W5CT_FP32_BULK 1           /* flux, eigen and WENO arithmetic in float;
+                                      RK stage accumulation, CT EMF accumulation
+                                      into the face field and all reductions in
+                                      double */
+
+typedef struct w5ct_ctx w5ct_ctx;
+
+typedef struct {
+    double gamma;        /* adiabatic index (5/3 in the paper's tests) */
+    double cfl;          /* Courant number of Eq. (cfl) (0.8 in the paper) */
+    int weno_variant;    /* W5CT_WENO_JS or W5CT_WENO_Z */
+    int precision;       /* W5CT_FP64 or W5CT_FP32_BULK */
+    double eps_js;       /* JS epsilon, 1e-6 (Sec. 2.2) */
+    double eps_z;        /* WENO-Z epsilon, 1e-40 (Sec. 2.2); FP32_BULK uses
+                            max(eps_z, 1e-30) because 1e-40 is subnormal in float */
+    double eps_b;        /* degeneracy threshold eps_B, 1e-30 (Appendix A) */
+    int floors;          /* 0: none (the paper's default, Sec. 4); 1: rho and P
+                            are floored inside primitive recovery only */
+    double rho_min;      /* density floor when floors = 1 */
+    double p_min;        /* pressure floor when floors = 1 */
+    void *stream;        /* cudaStream_t for all device work; NULL = default */
+} w5ct_config;
+
+/* Fill *cfg with the paper's defaults: gamma 5/3, CFL 0.8, WENO-Z, FP64,
+ * eps 1e-6 / 1e-40 / 1e-30, no floors, default stream. */
+int w5ct_config_default(w5ct_config *cfg);
+
+/* Create a context on the current CUDA device.  *out receives the handle.
+ * Errors: W5CT_ERR_ARG for a null pointer, gamma <= 1, cfl <= 0 or an
+ * unknown variant / precision. */
+int w5ct_create(const w5ct_config *cfg, w5ct_ctx **out);
+
+/* Free every device buffer and the context.  ctx may be NULL. */
+int w5ct_destroy(w5ct_ctx *ctx);
+
+/* Replace the stream all later device work is enqueued on. */
+int w5ct_set_stream(w5ct_ctx *ctx, void *stream);
+
+/* Allocate one periodic patch (the paper's patch, Sec. 3).  npatch must be
+ * 1 (W5CT_ERR_UNSUPPORTED otherwise); n3 = {nx, ny, nz}, each >= 1;
+ * dx3 = {dx, dy, dz} > 0 (host pointers).  Previous buffers are freed. */
+int w5ct_init_grid(w5ct_ctx *ctx, int npatch, const int *n3, const double *dx3);
+
+/* Load the state q^n: cons (5 planes) and bface (3 planes), host or device
+ * (on_device).  patch must be 0.  The face field should be discretely
+ * divergence-free; the scheme keeps its divergence at round-off (Sec. 2.3)
+ * but does not remove an initial one. */
+int w5ct_set_state(w5ct_ctx *ctx, int patch, const double *cons, const double *bface, int on_device);
+
+/* Read the state back; any of cons / bface / bcell may be NULL.  Synchronises.
+ * Returns W5CT_ERR_NONPHYSICAL if a step since the last check met a
+ * non-physical state (the buffers are still written). */
+int w5ct_get_state(w5ct_ctx *ctx, int patch, double *cons, double *bface, double *bcell, int on_device);
+
+/* One full RK4 + CT step of size dt > 0 (Secs. 2.1, 2.3, 3.1.3): four
+ * stages of x-, y- and z-sweeps of the characteristic WENO flux, the
+ * transport-flux corrections and corner EMFs, the face-field update and
+ * the fourth-order face-to-centre interpolation.  Asynchronous. */
+int w5ct_step(w5ct_ctx *ctx, double dt);
+
+/* As w5ct_step with dt read from device memory at *dt_dev (one double,
+ * read by the kernels when they run), so a sequence of steps can be
+ * captured in a CUDA graph. */
+int w5ct_step_dev(w5ct_ctx *ctx, const double *dt_dev);
+
+/* One step with dt = CFL / sum_d (S_d / dx_d) computed on the device from
+ * the current state (Eq. cfl, with S_d from w5ct_max_signal_speed); no
+ * host synchronisation.  If dt_dev_out is not NULL the dt used is also
+ * written there (device pointer, one double). */
+int w5ct_step_cfl(w5ct_ctx *ctx, double *dt_dev_out);
+
+/* S_d = max over cells of |v_d| + c_fast^d for d = x, y, z (Eq. cfl; the
+ * fast speed of Eq. fast with B_n = B_d), out[3] on the host.  Synchronises.
+ * FP32_BULK evaluates the speeds in float. */
+int w5ct_max_signal_speed(w5ct_ctx *ctx, int patch, double out[3]);
+
+/* dt = CFL / sum_d (S_d / dx_d) on the host.  Synchronises. */
+int w5ct_cfl_dt(w5ct_ctx *ctx, double *dt);
+
+/* Discrete divergence of the face field at cell centres,
+ * (b_x(i) - b_x(i-1))/dx + (b_y(j) - b_y(j-1))/dy + (b_z(k) - b_z(k-1))/dz:
+ * *linf its maximum modulus, *l2 its root mean square.  FP64, deterministic.
+ * Synchronises. */
+int w5ct_div_b_norm(w5ct_ctx *ctx, int patch, double *linf, double *l2);
+
+/* Volume integrals (sum * dx*dy*dz) of rho, m_x, m_y, m_z, E, b_x, b_y, b_z
+ * in out[8] (host).  FP64, fixed summation order (deterministic).
+ * Synchronises. */
+int w5ct_conserved_totals(w5ct_ctx *ctx, int patch, double out[8]);
+
+/* Number of floor activations (when floors = 1) and the non-physical flag
+ * since the last set_state; either pointer may be NULL.  Synchronises. */
+int w5ct_status(w5ct_ctx *ctx, long long *floor_hits, int *nonphysical);
+
+/* Block the host until all work of the context's stream is done. */
+int w5ct_synchronize(w5ct_ctx *ctx);
+
+/* Kernel timing: when enabled, each launch of the characteristic sweep
+ * kernel is bracketed by CUDA events on the context's stream.
+ * w5ct_sweep_timing returns the number of sweep launches and their summed
+ * device time in milliseconds since timing was last enabled (synchronises). */
+int w5ct_set_timing(w5ct_ctx *ctx, int enable);
+int w5ct_sweep_timing(w5ct_ctx *ctx, long long *launches, double *total_ms);
+
+/* Number of kernel launches the context has issued since it was created. */
+int w5ct_launch_count(w5ct_ctx *ctx, long long *launches);
+
+/* Text of the last error of ctx (or of the last failed w5ct_create when ctx
+ * is NULL).  Never NULL; valid until the next call on ctx. */
+const char *w5ct_last_error(const w5ct_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* W5CT_H */

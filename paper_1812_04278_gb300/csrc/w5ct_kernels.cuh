@@ -1,0 +1,409 @@
+// w5ct_kernels.cuh -- CUDA kernels of one RK4 + CT step (sm_103a).
+//
+// Data layout in HBM (one periodic patch, x fastest, one plane per field):
+//   FP64 state   q0[5] (rho, m, E), b0[3] (forward faces)   -- q^n, b^n
+//   FP64 accum.  acc[5] = sum_k w_k c_k D_k, oacc[3] = sum_k w'_k Omega_k
+//   Real stage   qs[5], bs[3] (stage state), bc[3] (cell-centred B)
+//   Real faces   F{x,y,z}[5] lab-ordered face fluxes, S{x,y,z}[2] CT
+//                transport fluxes (x: f*_y, f*_z; y: g*_z, g*_x; z: h*_x, h*_y)
+// Real is double (FP64 path) or float (FP32-bulk path).
+//
+// Per stage:  cellb -> sweep<x> -> sweep<y> -> sweep<z> -> update<stage>.
+#pragma once
+#include <cstdint>
+
+#include "w5ct_physics.cuh"
+
+namespace w5ct {
+
+__device__ __forceinline__ int wrapi(int g, int n) {
+    if ((unsigned)g < (unsigned)n) return g;
+    const int r = g % n;
+    return r < 0 ? r + n : r;
+}
+
+// ======================================================================
+// characteristic sweep (Sec. 2.2 + Appendix A + Eqs. fct1-fct6)
+// ======================================================================
+
+template <typename Real>
+struct SweepArgs {
+    int nx, ny, nz;
+    const Real *q[5];
+    const Real *bc[3];
+    Real *F[5];
+    Real *S[2];
+    Phys<Real> K;
+    int *flag;
+    unsigned long long *hits;
+};
+
+// Tile of one block: 32 lanes along x always (coalesced loads and stores).
+//  x-sweep: 32 faces along x  x  T2 pencils along y
+//  y-sweep: 32 pencils along x  x  T2 faces along y
+//  z-sweep: 32 pencils along x  x  T2 faces along z
+// The cell box adds the 2 + 3 stencil cells along the sweep axis.
+template <int AX, int T2>
+struct SweepTile {
+    static constexpr int BX = 32;
+    static constexpr int BY = (AX == 2) ? 1 : T2;
+    static constexpr int BZ = (AX == 2) ? T2 : 1;
+    static constexpr int CX = BX + (AX == 0 ? 5 : 0);
+    static constexpr int CY = BY + (AX == 1 ? 5 : 0);
+    static constexpr int CZ = BZ + (AX == 2 ? 5 : 0);
+    static constexpr int NC = CX * CY * CZ;
+    static constexpr int ST = (AX == 0) ? 1 : (AX == 1) ? CX : CX * CY;
+    static constexpr int NT = 32 * T2;
+};
+
+template <int AX, typename Real, int VAR, int T2>
+__global__ void __launch_bounds__(32 * T2) sweep_kernel(SweepArgs<Real> a) {
+    using TT = SweepTile<AX, T2>;
+    extern __shared__ __align__(16) unsigned char w5ct_smem[];
+    Real *sm = reinterpret_cast<Real *>(w5ct_smem);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TT::BX, y0 = blockIdx.y * TT::BY, z0 = blockIdx.z * TT::BZ;
+    const int ox = x0 - (AX == 0 ? 2 : 0), oy = y0 - (AX == 1 ? 2 : 0), oz = z0 - (AX == 2 ? 2 : 0);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+
+    // phase 1: per-cell primitives, flux and speeds of the cell box
+    bool bad = false, hit = false;
+    for (int c = tid; c < TT::NC; c += TT::NT) {
+        const int cx = c % TT::CX;
+        const int cy = (c / TT::CX) % TT::CY;
+        const int cz = c / (TT::CX * TT::CY);
+        const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
+        const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+        cell_fill<Real, AX>(sm + c, TT::NC, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
+                            a.bc[0][g], a.bc[1][g], a.bc[2][g], a.K, bad, hit);
+    }
+    if (bad) atomicOr(a.flag, 1);
+    if (a.K.floors) {
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (threadIdx.x == 0 && m) atomicAdd(a.hits, (unsigned long long)__popc(m));
+    }
+    __syncthreads();
+
+    // phase 2: one interface per thread
+    const int bx = threadIdx.x;
+    const int by = (AX == 2) ? 0 : threadIdx.y;
+    const int bz = (AX == 2) ? threadIdx.y : 0;
+    const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+    if (gx < nx && gy < ny && gz < nz) {
+        const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
+        Real Ff[7], s1, s2;
+        face_flux<Real, VAR>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
+        const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+        a.F[0][g] = Ff[0];
+        a.F[1 + AX][g] = Ff[1];
+        a.F[1 + (AX + 1) % 3][g] = Ff[2];
+        a.F[1 + (AX + 2) % 3][g] = Ff[3];
+        a.F[4][g] = Ff[6];
+        a.S[0][g] = s1;
+        a.S[1][g] = s2;
+    }
+}
+
+// ======================================================================
+// cell-centred field: fourth-order interpolation of the faces (Sec. 2.3)
+// ======================================================================
+
+template <typename Real>
+__global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, const Real *__restrict__ bx,
+                                                    const Real *__restrict__ by, const Real *__restrict__ bz,
+                                                    Real *__restrict__ Bx, Real *__restrict__ By, Real *__restrict__ Bz) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    auto I = [&](int ii, int jj, int kk) -> size_t {
+        return (size_t)wrapi(ii, nx) + (size_t)nx * ((size_t)wrapi(jj, ny) + (size_t)ny * (size_t)wrapi(kk, nz));
+    };
+    const size_t p = I(i, j, k);
+    const Real s = Real(1.0 / 16.0);
+    Bx[p] = (Real(9) * (bx[I(i - 1, j, k)] + bx[p]) - (bx[I(i - 2, j, k)] + bx[I(i + 1, j, k)])) * s;
+    By[p] = (Real(9) * (by[I(i, j - 1, k)] + by[p]) - (by[I(i, j - 2, k)] + by[I(i, j + 1, k)])) * s;
+    Bz[p] = (Real(9) * (bz[I(i, j, k - 1)] + bz[p]) - (bz[I(i, j, k - 2)] + bz[I(i, j, k + 1)])) * s;
+}
+
+// ======================================================================
+// stage update: flux divergence (Eq. num), RK4 stage (Sec. 2.1), corner
+// EMFs (Eqs. ox1-ox3), face-field update (Sec. 2.3) and the final CT
+// update from the accumulated EMFs (Sec. 3.1.3)
+// ======================================================================
+
+template <typename Real>
+struct UpdateArgs {
+    int nx, ny, nz;
+    Real rdx, rdy, rdz;          // 1/dx etc. (stage arithmetic)
+    double drdx, drdy, drdz;     // 1/dx etc. (final FP64 curl)
+    const Real *Fx[5], *Fy[5], *Fz[5];
+    const Real *Sx[2], *Sy[2], *Sz[2];
+    double *q0[5], *acc[5], *b0[3], *oacc[3];
+    Real *qs[5], *bs[3];
+    const double *dt;
+};
+
+// stage factors c_k of Sec. 2.1 (1/2, 1/2, 1, 1/6) and the products w_k c_k
+// of the q_save weights (1/3, 2/3, 1/3, 1) with them, (1, 2, 2, 1)/6, which
+// are also the weights of the accumulated EMFs
+template <int S>
+struct StageW {
+    static constexpr double c = S == 0 ? 0.5 : S == 1 ? 0.5 : S == 2 ? 1.0 : 1.0 / 6.0;
+    static constexpr double wc = (S == 0 || S == 3) ? 1.0 / 6.0 : 1.0 / 3.0;
+};
+
+template <typename Real, int STAGE>
+__global__ void __launch_bounds__(256) update_kernel(UpdateArgs<Real> a) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const int im = i > 0 ? i - 1 : nx - 1, ip = i + 1 < nx ? i + 1 : 0;
+    const int jm = j > 0 ? j - 1 : ny - 1, jp = j + 1 < ny ? j + 1 : 0;
+    const int km = k > 0 ? k - 1 : nz - 1, kp = k + 1 < nz ? k + 1 : 0;
+    auto I = [&](int ii, int jj, int kk) -> size_t {
+        return (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * (size_t)kk);
+    };
+    const size_t p = I(i, j, k);
+    const double dt = *a.dt;
+    constexpr double c = StageW<STAGE>::c, wc = StageW<STAGE>::wc;
+
+    // ---- conserved fields
+    {
+        const size_t pxm = I(im, j, k), pym = I(i, jm, k), pzm = I(i, j, km);
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            const Real D = (a.Fx[f][pxm] - a.Fx[f][p]) * a.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * a.rdy +
+                           (a.Fz[f][pzm] - a.Fz[f][p]) * a.rdz;
+            const double d = (double)D;
+            const double q0 = a.q0[f][p];
+            if (STAGE < 3) {
+                a.qs[f][p] = (Real)(q0 + (c * dt) * d);
+                a.acc[f][p] = (STAGE == 0 ? 0.0 : a.acc[f][p]) + wc * d;
+            } else {
+                const double qn = q0 + dt * (a.acc[f][p] + wc * d);
+                a.q0[f][p] = qn;
+                a.qs[f][p] = (Real)qn;
+            }
+        }
+    }
+
+    // ---- corner EMFs (Eqs. ox1-ox3) from the transport fluxes
+    const Real *fy = a.Sx[0], *fz = a.Sx[1], *gz = a.Sy[0], *gx = a.Sy[1], *hx = a.Sz[0], *hy = a.Sz[1];
+    const Real h = Real(0.5);
+    // Omega_x at (ii+1/2, jj+1/2, k): g*_x averaged over i, f*_y over j
+    auto Ox = [&](int ii, int iip, int jj, int jjp, int kk) -> Real {
+        return h * (gx[I(ii, jj, kk)] + gx[I(iip, jj, kk)]) - h * (fy[I(ii, jj, kk)] + fy[I(ii, jjp, kk)]);
+    };
+    // Omega_y at (i, jj+1/2, kk+1/2): h*_y averaged over j, g*_z over k
+    auto Oy = [&](int ii, int jj, int jjp, int kk, int kkp) -> Real {
+        return h * (hy[I(ii, jj, kk)] + hy[I(ii, jjp, kk)]) - h * (gz[I(ii, jj, kk)] + gz[I(ii, jj, kkp)]);
+    };
+    // Omega_z at (ii+1/2, j, kk+1/2): f*_z averaged over k, h*_x over i
+    auto Oz = [&](int ii, int iip, int jj, int kk, int kkp) -> Real {
+        return h * (fz[I(ii, jj, kk)] + fz[I(ii, jj, kkp)]) - h * (hx[I(ii, jj, kk)] + hx[I(iip, jj, kk)]);
+    };
+    const Real ox_c = Ox(i, ip, j, jp, k);          // Omega_x(i, j, k)
+    const Real ox_jm = Ox(i, ip, jm, j, k);         // Omega_x(i, j-1, k)
+    const Real ox_im = Ox(im, i, j, jp, k);         // Omega_x(i-1, j, k)
+    const Real oy_c = Oy(i, j, jp, k, kp);          // Omega_y(i, j, k)
+    const Real oy_km = Oy(i, j, jp, km, k);         // Omega_y(i, j, k-1)
+    const Real oy_jm = Oy(i, jm, j, k, kp);         // Omega_y(i, j-1, k)
+    const Real oz_c = Oz(i, ip, j, k, kp);          // Omega_z(i, j, k)
+    const Real oz_km = Oz(i, ip, j, km, k);         // Omega_z(i, j, k-1)
+    const Real oz_im = Oz(im, i, j, k, kp);         // Omega_z(i-1, j, k)
+
+    if (STAGE < 3) {
+        // face equations of Sec. 2.3 with this stage's EMFs
+        const Real dbx = -(ox_c - ox_jm) * a.rdy + (oz_c - oz_km) * a.rdz;
+        const Real dby = -(oy_c - oy_km) * a.rdz + (ox_c - ox_im) * a.rdx;
+        const Real dbz = -(oz_c - oz_im) * a.rdx + (oy_c - oy_jm) * a.rdy;
+        const double cdt = c * dt;
+        a.bs[0][p] = (Real)(a.b0[0][p] + cdt * (double)dbx);
+        a.bs[1][p] = (Real)(a.b0[1][p] + cdt * (double)dby);
+        a.bs[2][p] = (Real)(a.b0[2][p] + cdt * (double)dbz);
+        a.oacc[0][p] = (STAGE == 0 ? 0.0 : a.oacc[0][p]) + wc * (double)ox_c;
+        a.oacc[1][p] = (STAGE == 0 ? 0.0 : a.oacc[1][p]) + wc * (double)oy_c;
+        a.oacc[2][p] = (STAGE == 0 ? 0.0 : a.oacc[2][p]) + wc * (double)oz_c;
+    } else {
+        // accumulated EMFs sum_k w'_k Omega_k, in double, at the nine edges
+        const double *Ax = a.oacc[0], *Ay = a.oacc[1], *Az = a.oacc[2];
+        const double ax_c = Ax[p] + wc * (double)ox_c;
+        const double ax_jm = Ax[I(i, jm, k)] + wc * (double)ox_jm;
+        const double ax_im = Ax[I(im, j, k)] + wc * (double)ox_im;
+        const double ay_c = Ay[p] + wc * (double)oy_c;
+        const double ay_km = Ay[I(i, j, km)] + wc * (double)oy_km;
+        const double ay_jm = Ay[I(i, jm, k)] + wc * (double)oy_jm;
+        const double az_c = Az[p] + wc * (double)oz_c;
+        const double az_km = Az[I(i, j, km)] + wc * (double)oz_km;
+        const double az_im = Az[I(im, j, k)] + wc * (double)oz_im;
+        const double dbx = -(ax_c - ax_jm) * a.drdy + (az_c - az_km) * a.drdz;
+        const double dby = -(ay_c - ay_km) * a.drdz + (ax_c - ax_im) * a.drdx;
+        const double dbz = -(az_c - az_im) * a.drdx + (ay_c - ay_jm) * a.drdy;
+        const double bxn = a.b0[0][p] + dt * dbx;
+        const double byn = a.b0[1][p] + dt * dby;
+        const double bzn = a.b0[2][p] + dt * dbz;
+        a.b0[0][p] = bxn;
+        a.b0[1][p] = byn;
+        a.b0[2][p] = bzn;
+        a.bs[0][p] = (Real)bxn;
+        a.bs[1][p] = (Real)byn;
+        a.bs[2][p] = (Real)bzn;
+    }
+}
+
+// ======================================================================
+// reductions
+// ======================================================================
+
+constexpr int kRedThreads = 256;
+
+template <typename T, int N>
+__device__ __forceinline__ void block_reduce(T (&v)[N], bool is_max[N], T *red /* N*32 */) {
+    // warp level
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T other = __shfl_xor_sync(0xffffffffu, v[q], o);
+            v[q] = is_max[q] ? (other > v[q] ? other : v[q]) : v[q] + other;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) red[q * 32 + warp] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            T x = lane < nw ? red[q * 32 + lane] : (is_max[q] ? T(0) : T(0));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T other = __shfl_xor_sync(0xffffffffu, x, o);
+                x = is_max[q] ? (other > x ? other : x) : x + other;
+            }
+            v[q] = x;
+        }
+    }
+}
+
+// |v_d| + c_f^d maxima of the stage state (Eq. cfl)
+template <typename Real>
+__global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx, int ny, const Real *q0, const Real *q1,
+                                                            const Real *q2, const Real *q3, const Real *q4,
+                                                            const Real *B0, const Real *B1, const Real *B2,
+                                                            Phys<Real> K, unsigned long long *smax, int *flag) {
+    __shared__ double red[3 * 32];
+    double v[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        Real r = q0[p];
+        if (K.floors && r < K.rho_min) r = K.rho_min;
+        const Real ir = M<Real>::rcp_(r);
+        const Real vx = q1[p] * ir, vy = q2[p] * ir, vz = q3[p] * ir;
+        const Real bx = B0[p], by = B1[p], bz = B2[p];
+        Real P = K.gm1 * (q4[p] - Real(0.5) * r * (vx * vx + vy * vy + vz * vz) - Real(0.5) * (bx * bx + by * by + bz * bz));
+        if (K.floors && P < K.p_min) P = K.p_min;
+        if (!(r > Real(0)) || !M<Real>::finite_pos(P)) bad = true;
+        v[0] = fmax(v[0], (double)signal_speed<Real>(r, vx, P, bx, by, bz, K));
+        v[1] = fmax(v[1], (double)signal_speed<Real>(r, vy, P, by, bz, bx, K));
+        v[2] = fmax(v[2], (double)signal_speed<Real>(r, vz, P, bz, bx, by, K));
+    }
+    if (bad) atomicOr(flag, 1);
+    bool ismax[3] = {true, true, true};
+    block_reduce<double, 3>(v, ismax, red);
+    if (threadIdx.x == 0) {
+        // non-negative doubles order like their bit patterns
+        atomicMax(&smax[0], (unsigned long long)__double_as_longlong(v[0]));
+        atomicMax(&smax[1], (unsigned long long)__double_as_longlong(v[1]));
+        atomicMax(&smax[2], (unsigned long long)__double_as_longlong(v[2]));
+    }
+}
+
+// dt = CFL / sum_d (S_d / dx_d)
+static __global__ void dt_kernel(const unsigned long long *smax, double cfl, double rdx, double rdy, double rdz,
+                          double *dt, double *dt_copy) {
+    const double s0 = __longlong_as_double((long long)smax[0]);
+    const double s1 = __longlong_as_double((long long)smax[1]);
+    const double s2 = __longlong_as_double((long long)smax[2]);
+    const double v = cfl / (s0 * rdx + s1 * rdy + s2 * rdz);
+    *dt = v;
+    if (dt_copy) *dt_copy = v;
+}
+
+static __global__ void set_scalar_kernel(double *dst, double v) { *dst = v; }
+
+// discrete div b: per-block max |div| and sum div^2
+static __global__ void __launch_bounds__(kRedThreads) divb_partial_kernel(int nx, int ny, int nz, const double *bx, const double *by,
+                                                                   const double *bz, double rdx, double rdy, double rdz,
+                                                                   double *part) {
+    __shared__ double red[2 * 32];
+    const long long n = (long long)nx * ny * nz;
+    double v[2] = {0.0, 0.0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx);
+        const long long r = p / nx;
+        const int j = (int)(r % ny), k = (int)(r / ny);
+        const long long pxm = p - i + (i > 0 ? i - 1 : nx - 1);
+        const long long pym = p + (long long)nx * ((j > 0 ? j - 1 : ny - 1) - j);
+        const long long pzm = p + (long long)nx * ny * ((k > 0 ? k - 1 : nz - 1) - k);
+        const double d = (bx[p] - bx[pxm]) * rdx + (by[p] - by[pym]) * rdy + (bz[p] - bz[pzm]) * rdz;
+        v[0] = fmax(v[0], fabs(d));
+        v[1] += d * d;
+    }
+    bool ismax[2] = {true, false};
+    block_reduce<double, 2>(v, ismax, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x + 0] = v[0];
+        part[2 * blockIdx.x + 1] = v[1];
+    }
+}
+
+// per-block sums of up to 8 planes
+static __global__ void __launch_bounds__(kRedThreads) sums_partial_kernel(long long n, int nplanes, const double *const *planes,
+                                                                   double *part) {
+    __shared__ double red[8 * 32];
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < 8; ++f)
+            if (f < nplanes) v[f] += planes[f][p];
+    }
+    bool ismax[8] = {false, false, false, false, false, false, false, false};
+    block_reduce<double, 8>(v, ismax, red);
+    if (threadIdx.x == 0)
+        for (int f = 0; f < nplanes; ++f) part[8 * blockIdx.x + f] = v[f];
+}
+
+// one block: combine nblk partial records of `stride` values in a fixed order;
+// value q is a max if (maxmask >> q) & 1, else a sum.
+static __global__ void __launch_bounds__(kRedThreads) finalize_kernel(const double *part, int nblk, int stride, int nval,
+                                                               unsigned maxmask, double *out) {
+    __shared__ double red[8 * 32];
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool ismax[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ismax[q] = (maxmask >> q) & 1u;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nval) {
+                const double x = part[(size_t)b * stride + q];
+                v[q] = ismax[q] ? fmax(v[q], x) : v[q] + x;
+            }
+        }
+    }
+    block_reduce<double, 8>(v, ismax, red);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < nval; ++q) out[q] = v[q];
+}
+
+// double -> Real copy of a plane
+template <typename Real>
+__global__ void __launch_bounds__(256) to_real_kernel(long long n, const double *src, Real *dst) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        dst[p] = (Real)src[p];
+}
+
+}  // namespace w5ct

@@ -1,0 +1,423 @@
+// w5ct_physics.cuh -- device arithmetic of the WENO5 + CT ideal-MHD scheme
+// of Donnert et al. (arXiv:1812.04278), templated on the arithmetic type
+// (double for the FP64 path, float for the FP32-bulk path).
+//
+//   cell_fill  : primitives (Eq. P), flux along the sweep axis (Eq. fluxes),
+//                wave speeds (Eqs. slow, fast, ca) of one cell.
+//   face_flux  : characteristic WENO5 / WENO5-Z flux at one interface
+//                (Sec. 2.2, Eq. FWENO) with the eigenvectors of Appendix A.
+//
+// Readings of the garbled passages (identical in the CPU oracle):
+//   P* = P + B^2/2; fast/slow speeds from the discriminant
+//   d = (c_s^2 - c_A^2)^2 + b_t^2 (b_t^2 + 2 c_A^2 + 2 c_s^2) without
+//   cancellation, c_slow^2 = c_s^2 c_A^2 / c_f^2; Appendix A's "slow" block is
+//   the Alfven pair (m = 2, 6) and its "Alfven" block the slow pair (m = 3, 5);
+//   upper signs for m <= 3; beta normalised by |B_t|; sgn(B_n) = +1 iff
+//   B_n >= eps_B; fast-mode left eigenvector with the 1/(2 c_s^2) factor on
+//   every component, gamma_1 alpha_f v^2 +- Gamma_f, -+ alpha_f c_f and
+//   + sqrt(rho) c_s alpha_s beta in the field rows; entropy right eigenvector
+//   energy row v^2/2; interface state = mean of the two cells' primitives;
+//   alpha(m) = max(|lambda_m(i)|, |lambda_m(i+1)|); WENO-Z weights
+//   d_k (1 + (tau_5/(eps_Z + IS_k))^2).
+#pragma once
+#include <cuda_runtime.h>
+#include <type_traits>
+
+namespace w5ct {
+
+// per-cell quantities kept in shared memory during a sweep (frame components)
+enum CellQ {
+    C_RHO = 0, C_VN, C_VT1, C_VT2, C_BN, C_BT1, C_BT2, C_P,   // primitives w
+    C_RHOQ, C_MN, C_MT1, C_MT2, C_E,                          // conserved u (rho, m, E)
+    C_F0, C_F1, C_F2, C_F3, C_F4, C_F5, C_F6,                 // flux along n
+    C_CF, C_CA, C_CSL,                                        // c_fast, c_Alfven, c_slow
+    NCQ
+};
+
+template <typename Real>
+struct Phys {
+    Real gamma, gm1, g1, g2;     // gamma, gamma-1, (gamma-1)/2, (gamma-2)/(gamma-1)
+    Real eps_w;                  // WENO epsilon (JS or Z, per the variant)
+    Real eps_b;                  // eps_B of Appendix A
+    Real eps_b2;                 // threshold on c_f^2 - c_slow^2 (eps_B^2, >= FLT_MIN in float)
+    Real rho_min, p_min;
+    int floors;
+};
+
+// ---------------------------------------------------------------- math helpers
+template <typename Real> struct M;
+template <> struct M<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+    static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+    static __device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e308; }
+};
+template <> struct M<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+    static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ bool finite_pos(float x) { return x > 0.0f && x < 3.0e38f; }
+};
+
+// ---------------------------------------------------------------- wave speeds
+// c_f^2 - c_s^2 (fmc) and c_s^2 - c_slow^2 (cms) without cancellation.
+template <typename Real>
+__device__ __forceinline__ void speeds(Real cs2, Real ca2, Real bt2, Real &fmc, Real &cms, Real &cf2, Real &csl2) {
+    using m = M<Real>;
+    const Real dd = (cs2 - ca2) * (cs2 - ca2) + bt2 * (bt2 + Real(2) * ca2 + Real(2) * cs2);
+    const Real sd = m::sqrt_(dd);
+    const Real aa = ca2 + bt2 - cs2;
+    if (aa >= Real(0)) {
+        fmc = Real(0.5) * (aa + sd);
+        cms = fmc > Real(0) ? m::div_(cs2 * bt2, fmc) : Real(0);
+    } else {
+        cms = Real(0.5) * (sd - aa);
+        fmc = cms > Real(0) ? m::div_(cs2 * bt2, cms) : Real(0);
+    }
+    cf2 = cs2 + fmc;
+    csl2 = cf2 > Real(0) ? m::div_(cs2 * ca2, cf2) : Real(0);
+}
+
+// ---------------------------------------------------------------- one cell
+// Fills the NCQ per-cell quantities of a cell for a sweep along axis AX
+// (frame (n, t1, t2) = (AX, AX+1, AX+2) mod 3).  sm points at the cell's
+// slot of quantity 0; quantities are `stride` elements apart.
+template <typename Real, int AX>
+__device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real mx, Real my, Real mz, Real E,
+                                          Real Bx, Real By, Real Bz, const Phys<Real> &K, bool &bad, bool &hit) {
+    using m = M<Real>;
+    constexpr int n = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
+    const Real mm[3] = {mx, my, mz};
+    const Real BB3[3] = {Bx, By, Bz};
+    Real r = rho;
+    if (K.floors && r < K.rho_min) { r = K.rho_min; hit = true; }
+    const Real ir = m::rcp_(r);
+    const Real vn = mm[n] * ir, v1 = mm[t1] * ir, v2 = mm[t2] * ir;
+    const Real Bn = BB3[n], B1 = BB3[t1], B2 = BB3[t2];
+    const Real vv = vn * vn + v1 * v1 + v2 * v2;
+    const Real BB = Bn * Bn + B1 * B1 + B2 * B2;
+    Real P = K.gm1 * (E - Real(0.5) * r * vv - Real(0.5) * BB);
+    if (K.floors && P < K.p_min) { P = K.p_min; hit = true; }
+    if (!(r > Real(0)) || !m::finite_pos(P)) bad = true;
+    const Real Pt = P + Real(0.5) * BB;
+    const Real vB = vn * Bn + v1 * B1 + v2 * B2;
+    sm[C_RHO * stride] = r;
+    sm[C_VN * stride] = vn;
+    sm[C_VT1 * stride] = v1;
+    sm[C_VT2 * stride] = v2;
+    sm[C_BN * stride] = Bn;
+    sm[C_BT1 * stride] = B1;
+    sm[C_BT2 * stride] = B2;
+    sm[C_P * stride] = P;
+    sm[C_RHOQ * stride] = rho;
+    sm[C_MN * stride] = mm[n];
+    sm[C_MT1 * stride] = mm[t1];
+    sm[C_MT2 * stride] = mm[t2];
+    sm[C_E * stride] = E;
+    sm[C_F0 * stride] = r * vn;
+    sm[C_F1 * stride] = r * vn * vn + Pt - Bn * Bn;
+    sm[C_F2 * stride] = r * vn * v1 - Bn * B1;
+    sm[C_F3 * stride] = r * vn * v2 - Bn * B2;
+    sm[C_F4 * stride] = B1 * vn - Bn * v1;
+    sm[C_F5 * stride] = B2 * vn - Bn * v2;
+    sm[C_F6 * stride] = (E + Pt) * vn - Bn * vB;
+    const Real cs2 = K.gamma * P * ir;
+    const Real ca2 = Bn * Bn * ir;
+    const Real bt2 = (B1 * B1 + B2 * B2) * ir;
+    Real fmc, cms, cf2, csl2;
+    speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+    sm[C_CF * stride] = m::sqrt_(cf2);
+    sm[C_CA * stride] = m::div_(m::abs_(Bn), m::sqrt_(r));
+    sm[C_CSL * stride] = m::sqrt_(csl2);
+}
+
+// fast signal speed |v_d| + c_f^d of a cell along axis d (Eq. cfl)
+template <typename Real>
+__device__ __forceinline__ Real signal_speed(Real r, Real vn, Real P, Real Bn, Real B1, Real B2, const Phys<Real> &K) {
+    using m = M<Real>;
+    const Real ir = m::rcp_(r);
+    const Real cs2 = K.gamma * P * ir;
+    const Real ca2 = Bn * Bn * ir;
+    const Real bt2 = (B1 * B1 + B2 * B2) * ir;
+    Real fmc, cms, cf2, csl2;
+    speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+    return m::abs_(vn) + m::sqrt_(cf2);
+}
+
+// ---------------------------------------------------------------- WENO
+// phi_N(a, b, c, d) of Sec. 2.2 with JS (VAR = 0) or WENO-Z (VAR = 1)
+// weights.  The weights are normalised by one division: in double the
+// common denominator of the three alpha_k; in float the alpha_k themselves
+// (reciprocals never overflow there, the WENO-Z ratio is clamped at 1e18).
+template <typename Real, int VAR>
+__device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) {
+    const Real x0 = a - b, x1 = a - Real(3) * b;
+    const Real IS0 = Real(13) * x0 * x0 + Real(3) * x1 * x1;
+    const Real y0 = b - c, y1 = b + c;
+    const Real IS1 = Real(13) * y0 * y0 + Real(3) * y1 * y1;
+    const Real z0 = c - d, z1 = Real(3) * c - d;
+    const Real IS2 = Real(13) * z0 * z0 + Real(3) * z1 * z1;
+    Real w0, w2;
+    if constexpr (std::is_same<Real, double>::value) {
+        const double s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
+        if constexpr (VAR == 0) {
+            const double p0 = s1 * s2, p1 = s0 * s2, p2 = s0 * s1;
+            const double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
+            const double inv = 1.0 / (q0 + 6.0 * q1 + 3.0 * q2);
+            w0 = q0 * inv;
+            w2 = 3.0 * q2 * inv;
+        } else {
+            const double tau = fabs(IS0 - IS2);
+            const double tt = tau * tau;
+            const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
+            const double A0 = (e0 + tt) * (e1 * e2);
+            const double A1 = 6.0 * (e1 + tt) * (e0 * e2);
+            const double A2 = 3.0 * (e2 + tt) * (e0 * e1);
+            const double inv = 1.0 / (A0 + A1 + A2);
+            w0 = A0 * inv;
+            w2 = A2 * inv;
+        }
+    } else {
+        const float s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
+        float a0, a1, a2;
+        if constexpr (VAR == 0) {
+            a0 = __fdividef(1.0f, s0 * s0);
+            a1 = __fdividef(6.0f, s1 * s1);
+            a2 = __fdividef(3.0f, s2 * s2);
+        } else {
+            const float tau = fabsf(IS0 - IS2);
+            const float r0 = fminf(tau * __fdividef(1.0f, s0), 1.0e18f);
+            const float r1 = fminf(tau * __fdividef(1.0f, s1), 1.0e18f);
+            const float r2 = fminf(tau * __fdividef(1.0f, s2), 1.0e18f);
+            a0 = 1.0f + r0 * r0;
+            a1 = 6.0f * (1.0f + r1 * r1);
+            a2 = 3.0f * (1.0f + r2 * r2);
+        }
+        const float inv = __fdividef(1.0f, a0 + a1 + a2);
+        w0 = a0 * inv;
+        w2 = a2 * inv;
+    }
+    return w0 * Real(1.0 / 3.0) * (a - Real(2) * b + c) + (w2 - Real(0.5)) * Real(1.0 / 6.0) * (b - Real(2) * c + d);
+}
+
+// Eq. (FWENO) for one characteristic field from its 11 projections:
+// P[0] = L.central, P[1..5] = L.dF at i-3/2 .. i+5/2, P[6..10] = L.du there.
+template <typename Real, int VAR>
+__device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps) {
+    const Real ha = Real(0.5) * alpha;
+    Real p[5], q[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        p[j] = Real(0.5) * P[1 + j] + ha * P[6 + j];
+        q[j] = Real(0.5) * P[1 + j] - ha * P[6 + j];
+    }
+    return P[0] - phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps) + phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps);
+}
+
+// One magnetosonic (fast or slow) pair of characteristic fields: the left
+// eigenvectors are Lc + Ls and Lc - Ls (Ls non-zero in rows 0..3), the right
+// ones Rc + Rs and Rc - Rs (Rs non-zero in rows 1, 2, 3, 6).  The first
+// call initialises the frame flux Ff.
+template <typename Real, int VAR>
+__device__ __forceinline__ void magnetosonic_pair(const Real (&X)[11][7], const Real (&Lc)[7], const Real (&Ls)[4],
+                                                  const Real (&Rc)[7], const Real (&Rs)[4], Real alu, Real all,
+                                                  Real eps, Real (&Ff)[7], bool first) {
+    Real Pu[11], Pl[11];
+#pragma unroll
+    for (int x = 0; x < 11; ++x) {
+        Real pc = Lc[0] * X[x][0];
+#pragma unroll
+        for (int c = 1; c < 7; ++c) pc += Lc[c] * X[x][c];
+        Real ps = Ls[0] * X[x][0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) ps += Ls[c] * X[x][c];
+        Pu[x] = pc + ps;
+        Pl[x] = pc - ps;
+    }
+    const Real Fu = weno_field<Real, VAR>(Pu, alu, eps);
+    const Real Fl = weno_field<Real, VAR>(Pl, all, eps);
+    const Real sum = Fu + Fl, dif = Fu - Fl;
+    if (first) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Ff[c] = sum * Rc[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Ff[c] += sum * Rc[c];
+    }
+    Ff[1] += dif * Rs[0];
+    Ff[2] += dif * Rs[1];
+    Ff[3] += dif * Rs[2];
+    Ff[6] += dif * Rs[3];
+}
+
+// ---------------------------------------------------------------- one face
+// Characteristic WENO flux at the face between stencil cells 2 and 3 of the
+// six cells at sm + k*st (k = 0..5); quantities are `ncell` elements apart.
+// Ff receives the frame flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and
+// s1, s2 the CT transport fluxes F_{B_t} + <B_n v_t> of Eqs. (fct1)-(fct6).
+template <typename Real, int VAR>
+__device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell, int st, const Phys<Real> &K,
+                                          Real (&Ff)[7], Real &s1, Real &s2) {
+    using m = M<Real>;
+#define SMQ(q, k) sm[(q) * ncell + (k) * st]
+    // physical central combination and differences (projection is linear)
+    Real X[11][7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        const int qF = C_F0 + c;
+        const Real f0 = SMQ(qF, 0), f1 = SMQ(qF, 1), f2 = SMQ(qF, 2), f3 = SMQ(qF, 3), f4 = SMQ(qF, 4), f5 = SMQ(qF, 5);
+        X[0][c] = (Real(7) * (f2 + f3) - (f1 + f4)) * Real(1.0 / 12.0);
+        X[1][c] = f1 - f0;
+        X[2][c] = f2 - f1;
+        X[3][c] = f3 - f2;
+        X[4][c] = f4 - f3;
+        X[5][c] = f5 - f4;
+        const int qU = c == 0 ? C_RHOQ : c == 1 ? C_MN : c == 2 ? C_MT1 : c == 3 ? C_MT2 : c == 4 ? C_BT1 : c == 5 ? C_BT2 : C_E;
+        const Real u0 = SMQ(qU, 0), u1 = SMQ(qU, 1), u2 = SMQ(qU, 2), u3 = SMQ(qU, 3), u4 = SMQ(qU, 4), u5 = SMQ(qU, 5);
+        X[6][c] = u1 - u0;
+        X[7][c] = u2 - u1;
+        X[8][c] = u3 - u2;
+        X[9][c] = u4 - u3;
+        X[10][c] = u5 - u4;
+    }
+    // interface state: mean of the primitives of cells i and i+1
+    const Real r = Real(0.5) * (SMQ(C_RHO, 2) + SMQ(C_RHO, 3));
+    const Real vn = Real(0.5) * (SMQ(C_VN, 2) + SMQ(C_VN, 3));
+    const Real vt1 = Real(0.5) * (SMQ(C_VT1, 2) + SMQ(C_VT1, 3));
+    const Real vt2 = Real(0.5) * (SMQ(C_VT2, 2) + SMQ(C_VT2, 3));
+    const Real Bn = Real(0.5) * (SMQ(C_BN, 2) + SMQ(C_BN, 3));
+    const Real Bt1 = Real(0.5) * (SMQ(C_BT1, 2) + SMQ(C_BT1, 3));
+    const Real Bt2 = Real(0.5) * (SMQ(C_BT2, 2) + SMQ(C_BT2, 3));
+    const Real P = Real(0.5) * (SMQ(C_P, 2) + SMQ(C_P, 3));
+    // Lax-Friedrichs speeds alpha(m) from the cell eigenvalues
+    const Real vL = SMQ(C_VN, 2), vR = SMQ(C_VN, 3);
+    const Real cfL = SMQ(C_CF, 2), cfR = SMQ(C_CF, 3);
+    const Real caL = SMQ(C_CA, 2), caR = SMQ(C_CA, 3);
+    const Real csL = SMQ(C_CSL, 2), csR = SMQ(C_CSL, 3);
+    const Real al_fm = m::max_(m::abs_(vL - cfL), m::abs_(vR - cfR));
+    const Real al_fp = m::max_(m::abs_(vL + cfL), m::abs_(vR + cfR));
+    const Real al_am = m::max_(m::abs_(vL - caL), m::abs_(vR - caR));
+    const Real al_ap = m::max_(m::abs_(vL + caL), m::abs_(vR + caR));
+    const Real al_sm = m::max_(m::abs_(vL - csL), m::abs_(vR - csR));
+    const Real al_sp = m::max_(m::abs_(vL + csL), m::abs_(vR + csR));
+    const Real al_e = m::max_(m::abs_(vL), m::abs_(vR));
+    // transport fluxes <B_n v_t> of the two cells
+    const Real bvt1 = Real(0.5) * (SMQ(C_BN, 2) * SMQ(C_VT1, 2) + SMQ(C_BN, 3) * SMQ(C_VT1, 3));
+    const Real bvt2 = Real(0.5) * (SMQ(C_BN, 2) * SMQ(C_VT2, 2) + SMQ(C_BN, 3) * SMQ(C_VT2, 3));
+#undef SMQ
+
+    // ---- eigen scalars at the interface state (Appendix A)
+    const Real ir = m::rcp_(r);
+    const Real cs2 = K.gamma * P * ir;
+    const Real ca2 = Bn * Bn * ir;
+    const Real btm = Bt1 * Bt1 + Bt2 * Bt2;
+    const Real bt2 = btm * ir;
+    Real fmc, cms, cf2, csl2;
+    speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+    const Real cf = m::sqrt_(cf2), csl = m::sqrt_(csl2), cs = m::sqrt_(cs2);
+    const Real dfs = fmc + cms;   // c_f^2 - c_slow^2
+    Real af, as;
+    if (dfs >= K.eps_b2) {
+        const Real idf = m::rcp_(dfs);
+        af = m::sqrt_(m::max_(cms * idf, Real(0)));
+        as = m::sqrt_(m::max_(fmc * idf, Real(0)));
+    } else {
+        af = Real(1);
+        as = Real(1);
+    }
+    Real b1, b2;
+    if (btm > K.eps_b) {
+        const Real ib = m::rcp_(m::sqrt_(btm));
+        b1 = Bt1 * ib;
+        b2 = Bt2 * ib;
+    } else {
+        b1 = Real(0.70710678118654752440);
+        b2 = Real(0.70710678118654752440);
+    }
+    const Real sg = (Bn >= K.eps_b) ? Real(1) : Real(-1);
+    const Real sr = m::sqrt_(r);
+    const Real isr = sr * ir;
+    const Real v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    const Real bv = b1 * vt1 + b2 * vt2;
+    const Real Gf = af * cf * vn - as * csl * sg * bv;
+    const Real Ga = sg * (b2 * vt1 - b1 * vt2);
+    const Real Gs = as * csl * vn + af * cf * sg * bv;
+    const Real ics2 = m::rcp_(cs2);
+    const Real pre = Real(0.5) * ics2;
+    const Real tau = K.gm1 * ics2;
+    const Real eps = K.eps_w;
+
+    // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
+    {
+        const Real k1 = -K.gm1 * af;
+        const Real Lc[7] = {pre * K.g1 * af * v2, pre * k1 * vn, pre * k1 * vt1, pre * k1 * vt2,
+                            pre * (k1 * Bt1 + sr * cs * as * b1), pre * (k1 * Bt2 + sr * cs * as * b2), pre * K.gm1 * af};
+        const Real Ls[4] = {pre * Gf, -pre * af * cf, pre * csl * as * b1 * sg, pre * csl * as * b2 * sg};
+        const Real Rc[7] = {af, af * vn, af * vt1, af * vt2, cs * as * b1 * isr, cs * as * b2 * isr,
+                            af * (Real(0.5) * v2 + cf2 - K.g2 * cs2)};
+        const Real Rs[4] = {-af * cf, csl * as * b1 * sg, csl * as * b2 * sg, -Gf};   // rows 1, 2, 3, 6
+        magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
+    }
+    // ---- slow pair: m = 3 (v - c_slow, upper sign) and m = 5 (v + c_slow)
+    {
+        const Real k2 = -K.gm1 * as;
+        const Real Lc[7] = {pre * K.g1 * as * v2, pre * k2 * vn, pre * k2 * vt1, pre * k2 * vt2,
+                            pre * (k2 * Bt1 - sr * cs * af * b1), pre * (k2 * Bt2 - sr * cs * af * b2), pre * K.gm1 * as};
+        const Real Ls[4] = {pre * Gs, -pre * as * csl, -pre * cf * af * b1 * sg, -pre * cf * af * b2 * sg};
+        const Real Rc[7] = {as, as * vn, as * vt1, as * vt2, -cs * af * b1 * isr, -cs * af * b2 * isr,
+                            as * (Real(0.5) * v2 + csl2 - K.g2 * cs2)};
+        const Real Rs[4] = {-as * csl, -cf * af * b1 * sg, -cf * af * b2 * sg, -Gs};
+        magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
+    }
+    // ---- Alfven pair: m = 2 (v - c_A, upper sign) and m = 6 (v + c_A)
+    {
+        // L = (Ga/2, 0, -b2 sg/2, b1 sg/2, -+ sr b2/2, +- sr b1/2, 0)
+        // R = (0, 0, -b2 sg, b1 sg, -+ b2/sr, +- b1/sr, -Ga)
+        const Real l0 = Real(0.5) * Ga, l2 = Real(-0.5) * b2 * sg, l3 = Real(0.5) * b1 * sg;
+        const Real l4 = Real(-0.5) * sr * b2, l5 = Real(0.5) * sr * b1;
+        Real Pu[11], Pl[11];
+#pragma unroll
+        for (int x = 0; x < 11; ++x) {
+            const Real pc = l0 * X[x][0] + l2 * X[x][2] + l3 * X[x][3];
+            const Real ps = l4 * X[x][4] + l5 * X[x][5];
+            Pu[x] = pc + ps;
+            Pl[x] = pc - ps;
+        }
+        const Real Fu = weno_field<Real, VAR>(Pu, al_am, eps);
+        const Real Fl = weno_field<Real, VAR>(Pl, al_ap, eps);
+        const Real sum = Fu + Fl, dif = Fu - Fl;
+        Ff[2] += sum * (-b2 * sg);
+        Ff[3] += sum * (b1 * sg);
+        Ff[6] += sum * (-Ga);
+        Ff[4] += dif * (-b2 * isr);
+        Ff[5] += dif * (b1 * isr);
+    }
+    // ---- entropy field: m = 4 (v)
+    {
+        const Real L[7] = {Real(1) - Real(0.5) * tau * v2, tau * vn, tau * vt1, tau * vt2, tau * Bt1, tau * Bt2, -tau};
+        Real Pe[11];
+#pragma unroll
+        for (int x = 0; x < 11; ++x) {
+            Real pc = L[0] * X[x][0];
+#pragma unroll
+            for (int c = 1; c < 7; ++c) pc += L[c] * X[x][c];
+            Pe[x] = pc;
+        }
+        const Real Fe = weno_field<Real, VAR>(Pe, al_e, eps);
+        Ff[0] += Fe;
+        Ff[1] += Fe * vn;
+        Ff[2] += Fe * vt1;
+        Ff[3] += Fe * vt2;
+        Ff[6] += Fe * (Real(0.5) * v2);
+    }
+    s1 = Ff[4] + bvt1;
+    s2 = Ff[5] + bvt2;
+}
+
+}  // namespace w5ct

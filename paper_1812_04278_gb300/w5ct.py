@@ -1,0 +1,297 @@
+"""ctypes binding of libw5ct (``include/w5ct.h``).
+
+Every C entry point is exposed under its own name with argument
+marshalling only; all arithmetic runs in the library's CUDA kernels.  A
+non-zero return code raises :class:`W5ctError` carrying the library's error
+text.  Device buffers passed with ``on_device=1`` are torch CUDA tensors
+(or raw device addresses); host buffers are numpy float64 arrays.
+
+Importing this module loads ``libw5ct.so`` from the package directory and
+raises ImportError if it has not been built (``__graft_entry__.build()``):
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libw5ct.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build()")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+W5CT_OK = 0
+W5CT_ERR_ARG = -1
+W5CT_ERR_CUDA = -2
+W5CT_ERR_STATE = -3
+W5CT_ERR_NONPHYSICAL = -4
+W5CT_ERR_UNSUPPORTED = -5
+W5CT_WENO_JS = 0
+W5CT_WENO_Z = 1
+W5CT_FP64 = 0
+W5CT_FP32_BULK = 1
+
+EXPORTED = [
+    "w5ct_config_default", "w5ct_create", "w5ct_destroy", "w5ct_set_stream", "w5ct_init_grid",
+    "w5ct_set_state", "w5ct_get_state", "w5ct_step", "w5ct_step_dev", "w5ct_step_cfl",
+    "w5ct_max_signal_speed", "w5ct_cfl_dt", "w5ct_div_b_norm", "w5ct_conserved_totals",
+    "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
+    "w5ct_launch_count", "w5ct_last_error",
+]
+
+
+class w5ct_config(ctypes.Structure):
+    _fields_ = [("gamma", c_double), ("cfl", c_double), ("weno_variant", c_int), ("precision", c_int),
+                ("eps_js", c_double), ("eps_z", c_double), ("eps_b", c_double), ("floors", c_int),
+                ("rho_min", c_double), ("p_min", c_double), ("stream", c_void_p)]
+
+
+_DP = POINTER(c_double)
+_VP = c_void_p
+_sig = {
+    "w5ct_config_default": [POINTER(w5ct_config)],
+    "w5ct_create": [POINTER(w5ct_config), POINTER(c_void_p)],
+    "w5ct_destroy": [_VP],
+    "w5ct_set_stream": [_VP, _VP],
+    "w5ct_init_grid": [_VP, c_int, POINTER(c_int), _DP],
+    "w5ct_set_state": [_VP, c_int, _VP, _VP, c_int],
+    "w5ct_get_state": [_VP, c_int, _VP, _VP, _VP, c_int],
+    "w5ct_step": [_VP, c_double],
+    "w5ct_step_dev": [_VP, _VP],
+    "w5ct_step_cfl": [_VP, _VP],
+    "w5ct_max_signal_speed": [_VP, c_int, _DP],
+    "w5ct_cfl_dt": [_VP, _DP],
+    "w5ct_div_b_norm": [_VP, c_int, _DP, _DP],
+    "w5ct_conserved_totals": [_VP, c_int, _DP],
+    "w5ct_status": [_VP, POINTER(c_longlong), POINTER(c_int)],
+    "w5ct_synchronize": [_VP],
+    "w5ct_set_timing": [_VP, c_int],
+    "w5ct_sweep_timing": [_VP, POINTER(c_longlong), _DP],
+    "w5ct_launch_count": [_VP, POINTER(c_longlong)],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = c_int
+_lib.w5ct_last_error.argtypes = [_VP]
+_lib.w5ct_last_error.restype = c_char_p
+
+
+class W5ctError(RuntimeError):
+    def __init__(self, code: int, where: str, text: str):
+        super().__init__(f"{where} returned {code}: {text}")
+        self.code = code
+
+
+def w5ct_last_error(ctx=None) -> str:
+    return _lib.w5ct_last_error(ctx).decode(errors="replace")
+
+
+def _check(rc: int, where: str, ctx=None):
+    if rc != 0:
+        raise W5ctError(rc, where, w5ct_last_error(ctx))
+
+
+def _addr(buf):
+    """Address of a torch tensor, numpy array or integer; None -> NULL."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        assert buf.dtype == np.float64 and buf.flags.c_contiguous
+        return buf.ctypes.data
+    # torch tensor
+    assert buf.is_contiguous() and str(buf.dtype) == "torch.float64"
+    return buf.data_ptr()
+
+
+# ------------------------------------------------------------------ entry points
+
+
+def w5ct_config_default() -> w5ct_config:
+    cfg = w5ct_config()
+    _check(_lib.w5ct_config_default(ctypes.byref(cfg)), "w5ct_config_default")
+    return cfg
+
+
+def w5ct_create(cfg: w5ct_config):
+    h = c_void_p()
+    _check(_lib.w5ct_create(ctypes.byref(cfg), ctypes.byref(h)), "w5ct_create")
+    return h
+
+
+def w5ct_destroy(ctx):
+    _check(_lib.w5ct_destroy(ctx), "w5ct_destroy")
+
+
+def w5ct_set_stream(ctx, stream: int):
+    _check(_lib.w5ct_set_stream(ctx, stream), "w5ct_set_stream", ctx)
+
+
+def w5ct_init_grid(ctx, n3, dx3, npatch: int = 1):
+    n = (c_int * 3)(*[int(v) for v in n3])
+    d = (c_double * 3)(*[float(v) for v in dx3])
+    _check(_lib.w5ct_init_grid(ctx, npatch, n, d), "w5ct_init_grid", ctx)
+
+
+def w5ct_set_state(ctx, cons, bface, on_device: int, patch: int = 0):
+    _check(_lib.w5ct_set_state(ctx, patch, _addr(cons), _addr(bface), on_device), "w5ct_set_state", ctx)
+
+
+def w5ct_get_state(ctx, cons, bface, bcell, on_device: int, patch: int = 0):
+    _check(_lib.w5ct_get_state(ctx, patch, _addr(cons), _addr(bface), _addr(bcell), on_device),
+           "w5ct_get_state", ctx)
+
+
+def w5ct_step(ctx, dt: float):
+    _check(_lib.w5ct_step(ctx, float(dt)), "w5ct_step", ctx)
+
+
+def w5ct_step_dev(ctx, dt_dev):
+    _check(_lib.w5ct_step_dev(ctx, _addr(dt_dev)), "w5ct_step_dev", ctx)
+
+
+def w5ct_step_cfl(ctx, dt_dev_out=None):
+    _check(_lib.w5ct_step_cfl(ctx, _addr(dt_dev_out)), "w5ct_step_cfl", ctx)
+
+
+def w5ct_max_signal_speed(ctx, patch: int = 0) -> np.ndarray:
+    out = (c_double * 3)()
+    _check(_lib.w5ct_max_signal_speed(ctx, patch, out), "w5ct_max_signal_speed", ctx)
+    return np.array(out[:])
+
+
+def w5ct_cfl_dt(ctx) -> float:
+    out = c_double()
+    _check(_lib.w5ct_cfl_dt(ctx, ctypes.byref(out)), "w5ct_cfl_dt", ctx)
+    return out.value
+
+
+def w5ct_div_b_norm(ctx, patch: int = 0):
+    a, b = c_double(), c_double()
+    _check(_lib.w5ct_div_b_norm(ctx, patch, ctypes.byref(a), ctypes.byref(b)), "w5ct_div_b_norm", ctx)
+    return a.value, b.value
+
+
+def w5ct_conserved_totals(ctx, patch: int = 0) -> np.ndarray:
+    out = (c_double * 8)()
+    _check(_lib.w5ct_conserved_totals(ctx, patch, out), "w5ct_conserved_totals", ctx)
+    return np.array(out[:])
+
+
+def w5ct_status(ctx):
+    h, f = c_longlong(), c_int()
+    _check(_lib.w5ct_status(ctx, ctypes.byref(h), ctypes.byref(f)), "w5ct_status", ctx)
+    return h.value, f.value
+
+
+def w5ct_synchronize(ctx):
+    _check(_lib.w5ct_synchronize(ctx), "w5ct_synchronize", ctx)
+
+
+def w5ct_set_timing(ctx, enable: bool):
+    _check(_lib.w5ct_set_timing(ctx, int(bool(enable))), "w5ct_set_timing", ctx)
+
+
+def w5ct_sweep_timing(ctx):
+    n, ms = c_longlong(), c_double()
+    _check(_lib.w5ct_sweep_timing(ctx, ctypes.byref(n), ctypes.byref(ms)), "w5ct_sweep_timing", ctx)
+    return n.value, ms.value
+
+
+def w5ct_launch_count(ctx) -> int:
+    n = c_longlong()
+    _check(_lib.w5ct_launch_count(ctx, ctypes.byref(n)), "w5ct_launch_count", ctx)
+    return n.value
+
+
+# ------------------------------------------------------------------ convenience
+
+
+def make_config(precision=W5CT_FP64, weno_variant=W5CT_WENO_Z, gamma=5.0 / 3.0, cfl=0.8, floors=0,
+                rho_min=1e-8, p_min=1e-8, stream=None, eps_js=1e-6, eps_z=1e-40, eps_b=1e-30) -> w5ct_config:
+    cfg = w5ct_config_default()
+    cfg.precision = precision
+    cfg.weno_variant = weno_variant
+    cfg.gamma = gamma
+    cfg.cfl = cfl
+    cfg.floors = floors
+    cfg.rho_min = rho_min
+    cfg.p_min = p_min
+    cfg.eps_js = eps_js
+    cfg.eps_z = eps_z
+    cfg.eps_b = eps_b
+    cfg.stream = stream
+    return cfg
+
+
+class Solver:
+    """One periodic patch on the GPU: owns a context and forwards to the C ABI."""
+
+    def __init__(self, shape, dx, cfg: w5ct_config | None = None, stream: int | None = None):
+        cfg = cfg if cfg is not None else make_config()
+        if stream is not None:
+            cfg.stream = stream
+        self.cfg = cfg
+        self.ctx = w5ct_create(cfg)
+        self.shape = tuple(int(s) for s in shape)
+        self.dx = tuple(float(d) for d in (dx if not np.isscalar(dx) else (dx, dx, dx)))
+        self.n = self.shape[0] * self.shape[1] * self.shape[2]
+        w5ct_init_grid(self.ctx, self.shape, self.dx)
+
+    def close(self):
+        if self.ctx:
+            w5ct_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, cons, bface):
+        if isinstance(cons, np.ndarray):
+            cons = np.ascontiguousarray(cons, dtype=np.float64)
+            bface = np.ascontiguousarray(bface, dtype=np.float64)
+            assert cons.size == 5 * self.n and bface.size == 3 * self.n
+            w5ct_set_state(self.ctx, cons, bface, 0)
+        else:
+            assert cons.is_cuda and cons.numel() == 5 * self.n and bface.numel() == 3 * self.n
+            w5ct_set_state(self.ctx, cons.contiguous(), bface.contiguous(), 1)
+
+    def get_state(self):
+        nx, ny, nz = self.shape
+        cons = np.empty((5, nz, ny, nx))
+        bface = np.empty((3, nz, ny, nx))
+        bcell = np.empty((3, nz, ny, nx))
+        w5ct_get_state(self.ctx, cons, bface, bcell, 0)
+        return cons, bface, bcell
+
+    def step(self, dt: float):
+        w5ct_step(self.ctx, dt)
+
+    def step_cfl(self, dt_dev_out=None):
+        w5ct_step_cfl(self.ctx, dt_dev_out)
+
+    def max_signal_speed(self):
+        return w5ct_max_signal_speed(self.ctx)
+
+    def cfl_dt(self):
+        return w5ct_cfl_dt(self.ctx)
+
+    def div_b_norm(self):
+        return w5ct_div_b_norm(self.ctx)
+
+    def conserved_totals(self):
+        return w5ct_conserved_totals(self.ctx)
+
+    def status(self):
+        return w5ct_status(self.ctx)
+
+    def synchronize(self):
+        w5ct_synchronize(self.ctx)
