@@ -18,6 +18,10 @@ HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# The float sweep (FP32-bulk arithmetic) uses the hardware approximate
+# reciprocal / square root and flushes subnormals; every double operation
+# and every other translation unit stays IEEE.
+TU_FLAGS = {"w5ct_sweep32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _newest_input() -> float:
@@ -33,7 +37,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *CFLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC, *ARCH, *CFLAGS, *TU_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

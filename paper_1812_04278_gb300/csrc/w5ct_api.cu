@@ -445,7 +445,7 @@ int w5ct_step_cfl(w5ct_ctx *c, double *dt_dev_out) {
     if (rc) return rc;
     rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
     if (rc) return rc;
-    dt_kernel<<<1, 1, 0, c->stream>>>(c->smax, c->cfg.cfl, 1.0 / c->dx, 1.0 / c->dy, 1.0 / c->dz, c->dt_dev, dt_dev_out);
+    dt_kernel<<<1, 1, 0, c->stream>>>(c->smax, c->cfg.cfl, c->dx, c->dy, c->dz, c->dt_dev, dt_dev_out);
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
     return step_impl(c, c->dt_dev, true);

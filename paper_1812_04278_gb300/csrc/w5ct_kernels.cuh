@@ -38,13 +38,16 @@ struct SweepArgs {
     unsigned long long *hits;
 };
 
-// Tile of one block: 32 lanes along x always (coalesced loads and stores).
+// Tile of one block of 32 x 8 threads: 32 lanes along x always (coalesced
+// loads and stores), T2 (a multiple of 8) faces in the second direction,
+// each thread computing T2/8 faces.
 //  x-sweep: 32 faces along x  x  T2 pencils along y
 //  y-sweep: 32 pencils along x  x  T2 faces along y
 //  z-sweep: 32 pencils along x  x  T2 faces along z
 // The cell box adds the 2 + 3 stencil cells along the sweep axis.
 template <int AX, int T2>
 struct SweepTile {
+    static_assert(T2 % 8 == 0, "tile height must be a multiple of 8");
     static constexpr int BX = 32;
     static constexpr int BY = (AX == 2) ? 1 : T2;
     static constexpr int BZ = (AX == 2) ? T2 : 1;
@@ -53,11 +56,12 @@ struct SweepTile {
     static constexpr int CZ = BZ + (AX == 2 ? 5 : 0);
     static constexpr int NC = CX * CY * CZ;
     static constexpr int ST = (AX == 0) ? 1 : (AX == 1) ? CX : CX * CY;
-    static constexpr int NT = 32 * T2;
+    static constexpr int NT = 256;
+    static constexpr int FPT = T2 / 8;    // faces per thread
 };
 
-template <int AX, typename Real, int VAR, int T2>
-__global__ void __launch_bounds__(32 * T2) sweep_kernel(SweepArgs<Real> a) {
+template <int AX, typename Real, int VAR, int T2, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
     using TT = SweepTile<AX, T2>;
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     Real *sm = reinterpret_cast<Real *>(w5ct_smem);
@@ -84,23 +88,27 @@ __global__ void __launch_bounds__(32 * T2) sweep_kernel(SweepArgs<Real> a) {
     }
     __syncthreads();
 
-    // phase 2: one interface per thread
-    const int bx = threadIdx.x;
-    const int by = (AX == 2) ? 0 : threadIdx.y;
-    const int bz = (AX == 2) ? threadIdx.y : 0;
-    const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
-    if (gx < nx && gy < ny && gz < nz) {
-        const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
-        Real Ff[7], s1, s2;
-        face_flux<Real, VAR>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
-        const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
-        a.F[0][g] = Ff[0];
-        a.F[1 + AX][g] = Ff[1];
-        a.F[1 + (AX + 1) % 3][g] = Ff[2];
-        a.F[1 + (AX + 2) % 3][g] = Ff[3];
-        a.F[4][g] = Ff[6];
-        a.S[0][g] = s1;
-        a.S[1][g] = s2;
+    // phase 2: T2/8 interfaces per thread
+#pragma unroll 1
+    for (int r = 0; r < TT::FPT; ++r) {
+        const int t2 = threadIdx.y + 8 * r;
+        const int bx = threadIdx.x;
+        const int by = (AX == 2) ? 0 : t2;
+        const int bz = (AX == 2) ? t2 : 0;
+        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+        if (gx < nx && gy < ny && gz < nz) {
+            const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
+            Real Ff[7], s1, s2;
+            face_flux<Real, VAR>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
+            const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+            a.F[0][g] = Ff[0];
+            a.F[1 + AX][g] = Ff[1];
+            a.F[1 + (AX + 1) % 3][g] = Ff[2];
+            a.F[1 + (AX + 2) % 3][g] = Ff[3];
+            a.F[4][g] = Ff[6];
+            a.S[0][g] = s1;
+            a.S[1][g] = s2;
+        }
     }
 }
 
@@ -321,13 +329,15 @@ __global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx,
     }
 }
 
-// dt = CFL / sum_d (S_d / dx_d)
-static __global__ void dt_kernel(const unsigned long long *smax, double cfl, double rdx, double rdy, double rdz,
-                          double *dt, double *dt_copy) {
+// dt = CFL / sum_d (S_d / dx_d), with the same rounded operations as the
+// host-side w5ct_cfl_dt (no contraction), so both give the same dt
+static __global__ void dt_kernel(const unsigned long long *smax, double cfl, double dx, double dy, double dz,
+                                 double *dt, double *dt_copy) {
     const double s0 = __longlong_as_double((long long)smax[0]);
     const double s1 = __longlong_as_double((long long)smax[1]);
     const double s2 = __longlong_as_double((long long)smax[2]);
-    const double v = cfl / (s0 * rdx + s1 * rdy + s2 * rdz);
+    const double sum = __dadd_rn(__dadd_rn(__ddiv_rn(s0, dx), __ddiv_rn(s1, dy)), __ddiv_rn(s2, dz));
+    const double v = __ddiv_rn(cfl, sum);
     *dt = v;
     if (dt_copy) *dt_copy = v;
 }

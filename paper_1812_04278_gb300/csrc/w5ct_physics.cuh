@@ -50,6 +50,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
     static __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
     static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
     static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
@@ -59,6 +60,7 @@ template <> struct M<float> {
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
     static __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
@@ -133,7 +135,7 @@ __device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real m
     Real fmc, cms, cf2, csl2;
     speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
     sm[C_CF * stride] = m::sqrt_(cf2);
-    sm[C_CA * stride] = m::div_(m::abs_(Bn), m::sqrt_(r));
+    sm[C_CA * stride] = m::abs_(Bn) * (m::sqrt_(r) * ir);     // |B_n| / sqrt(rho)
     sm[C_CSL * stride] = m::sqrt_(csl2);
 }
 
@@ -206,6 +208,38 @@ __device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) 
     return w0 * Real(1.0 / 3.0) * (a - Real(2) * b + c) + (w2 - Real(0.5)) * Real(1.0 / 6.0) * (b - Real(2) * c + d);
 }
 
+// double: phi_N = Nn / Dn with the weights' common denominator Dn, so that
+// the two interpolants of one field can share a single division.
+template <int VAR>
+__device__ __forceinline__ void phi_nd(double a, double b, double c, double d, double eps, double &Nn, double &Dn) {
+    const double x0 = a - b, x1 = a - 3.0 * b;
+    const double IS0 = 13.0 * x0 * x0 + 3.0 * x1 * x1;
+    const double y0 = b - c, y1 = b + c;
+    const double IS1 = 13.0 * y0 * y0 + 3.0 * y1 * y1;
+    const double z0 = c - d, z1 = 3.0 * c - d;
+    const double IS2 = 13.0 * z0 * z0 + 3.0 * z1 * z1;
+    const double s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
+    double W0, W2;
+    if constexpr (VAR == 0) {
+        // alpha_k = d_k / s_k^2 times (s0 s1 s2)^2
+        const double p0 = s1 * s2, p1 = s0 * s2, p2 = s0 * s1;
+        W0 = p0 * p0;
+        W2 = 3.0 * (p2 * p2);
+        Dn = W0 + 6.0 * (p1 * p1) + W2;
+    } else {
+        // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2
+        const double tau = fabs(IS0 - IS2);
+        const double tt = tau * tau;
+        const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
+        W0 = (e0 + tt) * (e1 * e2);
+        W2 = 3.0 * (e2 + tt) * (e0 * e1);
+        Dn = W0 + 6.0 * (e1 + tt) * (e0 * e2) + W2;
+    }
+    // phi = w0 (a - 2b + c)/3 + (w2 - 1/2)(b - 2c + d)/6 with w = W / Dn
+    const double t1 = a - 2.0 * b + c, t2 = b - 2.0 * c + d;
+    Nn = (1.0 / 3.0) * W0 * t1 + ((1.0 / 6.0) * W2 - (1.0 / 12.0) * Dn) * t2;
+}
+
 // Eq. (FWENO) for one characteristic field from its 11 projections:
 // P[0] = L.central, P[1..5] = L.dF at i-3/2 .. i+5/2, P[6..10] = L.du there.
 template <typename Real, int VAR>
@@ -217,7 +251,19 @@ __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real ep
         p[j] = Real(0.5) * P[1 + j] + ha * P[6 + j];
         q[j] = Real(0.5) * P[1 + j] - ha * P[6 + j];
     }
-    return P[0] - phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps) + phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps);
+    if constexpr (std::is_same<Real, double>::value) {
+        double Np, Dp, Nm, Dm;
+        phi_nd<VAR>(p[0], p[1], p[2], p[3], eps, Np, Dp);
+        phi_nd<VAR>(q[4], q[3], q[2], q[1], eps, Nm, Dm);
+        const double prod = Dp * Dm;
+        if (prod > 1e-290 && prod < 1e290) {
+            // -Np/Dp + Nm/Dm over the common denominator: one division
+            return P[0] + (Nm * Dp - Np * Dm) / prod;
+        }
+        return P[0] - Np / Dp + Nm / Dm;
+    } else {
+        return P[0] - phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps) + phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps);
+    }
 }
 
 // One magnetosonic (fast or slow) pair of characteristic fields: the left
@@ -333,7 +379,7 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     }
     Real b1, b2;
     if (btm > K.eps_b) {
-        const Real ib = m::rcp_(m::sqrt_(btm));
+        const Real ib = m::rsqrt_(btm);
         b1 = Bt1 * ib;
         b2 = Bt2 * ib;
     } else {

@@ -18,7 +18,8 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_void_p
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libw5ct.so")
+# W5CT_LIB may name an alternative build of the same library (same ABI)
+_LIB_PATH = os.environ.get("W5CT_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "libw5ct.so")
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build()")
 _lib = ctypes.CDLL(_LIB_PATH)
