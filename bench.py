@@ -36,14 +36,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic flop count per interface of one sweep (the paper's steps as
-# the oracle performs them: interface average, Appendix A eigensystem,
-# 6-point projection of F and q onto 7 fields, LF split and two phi_N per
-# field, back-projection, CT transport fluxes) and per cell of one sweep
-# (primitives, flux, three speeds).  Divisions and square roots count 1.
-FACE_FLOPS = 2720
-CELL_FLOPS = 60
+# Algorithmic flop counts, obtained by running the oracle's own source with a
+# counting scalar type (+, -, *, / and sqrt count 1; comparisons, max and
+# |x| count 0): per interface of one sweep (interface average, Appendix A
+# eigensystem, 6-point projection of F and q onto 7 fields, LF split and
+# two phi_N per field, back-projection, CT transport fluxes), per cell of
+# one sweep (primitives, flux, three speeds) and per zone-update of the
+# whole RK4 + CT step.  WENO-Z (the benchmarked variant).
+FACE_FLOPS = 2858
+CELL_FLOPS = 93
 SWEEP_FLOPS_PER_ZONE = FACE_FLOPS + CELL_FLOPS
+STEP_FLOPS_PER_ZONE = 36057
 # Peaks: FP32 from the unit counts (152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz);
 # FP64 from the published GB300 rate (1.25 TFLOP/s); measured copy bandwidth.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -58,7 +61,7 @@ def load_peaks():
         return {}
 
 
-def parse_args():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=50)
@@ -68,7 +71,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    p.add_argument("--ref-n", type=int, default=64, help="edge of the oracle's sample box (reference arm)")
+    return p.parse_args(argv)
 
 
 def workload_config(n):
@@ -152,9 +156,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-# DRAM traffic of one sweep launch per zone, from an ncu capture of the
-# kernel whose source hash is given (None until captured).
-SWEEP_TRAFFIC = {"fp64": None, "fp32": None}
+# DRAM bytes (read + write) per zone of one sweep launch, from ncu captures
+# at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
+# the sweep source with the given hash; scaled to a launch by the zone count
+# (traffic grows with the zones: one tile pass per zone).
+SWEEP_TRAFFIC = {"src": "49ce1afc02bedb52", "fp64": 106.38, "fp32": 44.97}
+
+
+def sweep_traffic(key, zones):
+    if SWEEP_TRAFFIC.get("src") != kernel_source_hash():
+        return None
+    return SWEEP_TRAFFIC[key] * zones
 
 
 def l1_error(a_cons, a_b, b_cons, b_b):
@@ -163,6 +175,22 @@ def l1_error(a_cons, a_b, b_cons, b_b):
     comps = [np.abs(a_cons[f] - b_cons[f]).sum() / n for f in range(5)] + \
             [np.abs(a_b[f] - b_b[f]).sum() / n for f in range(3)]
     return float(np.sqrt(np.sum(np.square(comps))))
+
+
+def max_over_ranks_of(x, dist, device):
+    """The largest value of x over all ranks (the slowest replica's time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, zones, steps, ms):
+    """Whole-job zone-updates/s of `world` independent replicas of `zones`
+    cells advanced `steps` steps in `ms` milliseconds (the slowest rank)."""
+    return world * zones * steps / (ms * 1e-3)
 
 
 def dist_setup(args):
@@ -189,7 +217,7 @@ def run_reference(args):
     import oracle
     from paper_1812_04278_gb300 import inputs
     oracle.build()
-    ns = 64
+    ns = args.ref_n
     cons, bface = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
                                          kmin=2, kmax=min(32, ns // 2 - 1))
     o = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
@@ -269,11 +297,7 @@ def run_native(args):
     barrier = (lambda: dist.barrier()) if dist is not None else None
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, dist, "cuda")
 
     # ---- FP64 (headline)
     nlog = args.warmup + args.steps
@@ -335,8 +359,8 @@ def run_native(args):
         return
 
     peaks = load_peaks()
-    value64 = world * zones * args.steps / (ms64 * 1e-3)
-    value32 = world * zones * args.steps / (ms32 * 1e-3)
+    value64 = replica_throughput(world, zones, args.steps, ms64)
+    value32 = replica_throughput(world, zones, args.steps, ms32)
     sweep_flops = SWEEP_FLOPS_PER_ZONE * zones
     ach64 = sweep_flops / (swms64 / nsw64 * 1e-3) / 1e12
     ach32 = sweep_flops / (swms32 / nsw32 * 1e-3) / 1e12
@@ -356,9 +380,11 @@ def run_native(args):
         "config": workload_config(n),
         "roofline": {"kernel": "sweep_kernel (FP64)", "bound": "alu", "achieved": ach64, "peak": PEAK_FP64_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
-                     "traffic": SWEEP_TRAFFIC["fp64"], "launch_ms": swms64 / nsw64,
+                     "traffic": sweep_traffic("fp64", zones), "launch_ms": swms64 / nsw64,
                      "algorithmic_flops_per_launch": sweep_flops,
-                     "peak_source": "published GB300 FP64 rate 1.25 TFLOP/s (probe measured 1.0 TFLOP/s DFMA)"},
+                     "step_tflops": STEP_FLOPS_PER_ZONE * value64 / world / 1e12,
+                     "peak_source": "GB300 FP64 unit count: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz = 1.26; "
+                                    "published 1.25 TFLOP/s (probe measured 1.0 TFLOP/s DFMA)"},
         "fp32_bulk": {
             "value": value32, "unit": "zone-updates/s", "ms_per_step": ms32 / args.steps, "dtype": "f32",
             "accumulate": "f64", "speedup_vs_fp64": value32 / value64,
@@ -366,7 +392,8 @@ def run_native(args):
             "error_steps": nlog,
             "roofline": {"kernel": "sweep_kernel (FP32)", "bound": "alu", "achieved": ach32,
                          "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
-                         "traffic": SWEEP_TRAFFIC["fp32"], "launch_ms": swms32 / nsw32,
+                         "traffic": sweep_traffic("fp32", zones), "launch_ms": swms32 / nsw32,
+                         "step_tflops": STEP_FLOPS_PER_ZONE * value32 / world / 1e12,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "gpu_launches": launches32,
         },
@@ -410,8 +437,8 @@ def cpu_baseline(args):
             "seconds": el}
 
 
-def main():
-    args = parse_args()
+def main(argv=None):
+    args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
     else:
