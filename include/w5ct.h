@@ -161,9 +161,37 @@ int w5ct_sweep_timing(w5ct_ctx *ctx, long long *launches, double *total_ms);
 /* Number of kernel launches the context has issued since it was created. */
 int w5ct_launch_count(w5ct_ctx *ctx, long long *launches);
 
-/* Text of the last error of ctx (or of the last failed w5ct_create when ctx
- * is NULL).  Never NULL; valid until the next call on ctx. */
+/* Text of the last error of ctx (or, when ctx is NULL, of the last failed
+ * call that has no context: w5ct_create, w5ct_conserved_totals_noalloc).
+ * Never NULL; valid until the next call on ctx. */
 const char *w5ct_last_error(const w5ct_ctx *ctx);
+
+/* Largest grid (cells) w5ct_conserved_totals_noalloc accepts: 512^3. */
+#define W5CT_NOALLOC_MAX_CELLS 134217728LL
+
+/* The reduction of w5ct_conserved_totals for callers that cannot allocate
+ * device memory: code running while a CUDA stream is being captured,
+ * frameworks that reserve all device memory at start-up and forbid later
+ * allocations, and real-time host loops that cannot take the implicit
+ * synchronisation of cudaMalloc.  The paper has no counterpart; it is a
+ * convenience of this library.
+ *   cons   device pointer, 5 planes of nx*ny*nz doubles (rho, m_x, m_y, m_z, E)
+ *   bface  device pointer, 3 planes (b_x, b_y, b_z on the forward faces)
+ *   out    host pointer to 8 doubles: the volume integrals, as in
+ *          w5ct_conserved_totals (fixed summation order, deterministic)
+ *   stream cudaStream_t the work is enqueued on (NULL = default); the call
+ *          synchronises it before returning.
+ * No context is needed and nothing is allocated: the partial sums live in a
+ * fixed 512 KB device array inside the library, which every GPU that loads
+ * the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Errors: W5CT_ERR_ARG for null
+ * pointers, sizes < 1, spacings <= 0 or more than W5CT_NOALLOC_MAX_CELLS
+ * cells (text via w5ct_last_error(NULL)); W5CT_ERR_CUDA. */
+int w5ct_conserved_totals_noalloc(const double *cons, const double *bface, int nx, int ny, int nz,
+                                  double dx, double dy, double dz, double out[8], void *stream);
 
 #ifdef __cplusplus
 }

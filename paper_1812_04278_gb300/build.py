@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libw5ct.so")
-SOURCES = ["w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu"]
+SOURCES = ["w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_noalloc.cu"]
 HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -16,6 +16,8 @@ constexpr int kRedBlocks = 1024;     // partial-record count of the deterministi
 thread_local char g_create_err[512] = "no error";
 }  // namespace
 
+void w5ct::set_global_error(const char *text) { snprintf(g_create_err, sizeof(g_create_err), "%s", text); }
+
 struct w5ct_ctx {
     w5ct_config cfg;
     cudaStream_t stream = nullptr;

@@ -6,6 +6,9 @@
 
 namespace w5ct {
 
+// Record the text that w5ct_last_error(NULL) returns (calls without a context).
+void set_global_error(const char *text);
+
 // Launch the characteristic sweep along `axis` (0, 1, 2) with WENO variant
 // `variant` (0 = JS, 1 = Z).  Defined in w5ct_sweep32.cu / w5ct_sweep64.cu.
 template <typename Real>

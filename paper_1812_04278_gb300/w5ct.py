@@ -40,8 +40,9 @@ EXPORTED = [
     "w5ct_set_state", "w5ct_get_state", "w5ct_step", "w5ct_step_dev", "w5ct_step_cfl",
     "w5ct_max_signal_speed", "w5ct_cfl_dt", "w5ct_div_b_norm", "w5ct_conserved_totals",
     "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
-    "w5ct_launch_count", "w5ct_last_error",
+    "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc",
 ]
+W5CT_NOALLOC_MAX_CELLS = 134217728
 
 
 class w5ct_config(ctypes.Structure):
@@ -72,6 +73,7 @@ _sig = {
     "w5ct_set_timing": [_VP, c_int],
     "w5ct_sweep_timing": [_VP, POINTER(c_longlong), _DP],
     "w5ct_launch_count": [_VP, POINTER(c_longlong)],
+    "w5ct_conserved_totals_noalloc": [_VP, _VP, c_int, c_int, c_int, c_double, c_double, c_double, _DP, _VP],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -208,6 +210,16 @@ def w5ct_launch_count(ctx) -> int:
     n = c_longlong()
     _check(_lib.w5ct_launch_count(ctx, ctypes.byref(n)), "w5ct_launch_count", ctx)
     return n.value
+
+
+def w5ct_conserved_totals_noalloc(cons_dev, bface_dev, n3, dx3, stream=None) -> np.ndarray:
+    """Totals of caller-owned device arrays without any device allocation
+    (see include/w5ct.h); cons_dev / bface_dev are device buffers."""
+    out = (c_double * 8)()
+    _check(_lib.w5ct_conserved_totals_noalloc(_addr(cons_dev), _addr(bface_dev), int(n3[0]), int(n3[1]), int(n3[2]),
+                                               float(dx3[0]), float(dx3[1]), float(dx3[2]), out, stream),
+           "w5ct_conserved_totals_noalloc")
+    return np.array(out[:])
 
 
 # ------------------------------------------------------------------ convenience
