@@ -72,6 +72,10 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-n", type=int, default=64, help="edge of the oracle's sample box (reference arm)")
+    p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave"],
+                   help="turb: 256^3 turbulence (default); blast: blast in Mach-5 turbulence (use --n 512); "
+                        "wave: the 32^3 fast eigenmode (use --n 32 --steps 20)")
+    p.add_argument("--err-steps", type=int, default=5, help="FP64 steps of the blast error statement")
     return p.parse_args(argv)
 
 
@@ -249,9 +253,9 @@ def run_reference(args):
 
 
 def timed_run(torch, w5, shape, dx, cons_d, bface_d, precision, steps, warmup, dt_log=None, sampler=None,
-              barrier=None):
+              barrier=None, variant=1, floors=0):
     stream = torch.cuda.current_stream()
-    s = w5.Solver(shape, dx, w5.make_config(precision=precision, weno_variant=w5.W5CT_WENO_Z),
+    s = w5.Solver(shape, dx, w5.make_config(precision=precision, weno_variant=variant, floors=floors),
                   stream=stream.cuda_stream)
     s.set_state(cons_d, bface_d)
     for k in range(warmup):
@@ -437,10 +441,117 @@ def cpu_baseline(args):
             "seconds": el}
 
 
+def run_blast(args):
+    """Magnetised blast in Mach-5 turbulence (beta 0.2, P 0.1 -> 100 inside
+    r < 0.05), WENO-JS, floors on (rho, P >= 1e-8): FP32-bulk timed; the L1
+    error against FP64 after --err-steps steps at the FP64 run's dt sequence."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_04278_gb300 import build, inputs
+    build.build()
+    from paper_1812_04278_gb300 import w5ct as w5
+    n = args.n
+    shape, dx, zones = (n, n, n), (1.0 / n,) * 3, n ** 3
+    cons, bface = inputs.blast_turbulence_state(n)
+    cons_d, bface_d = torch.from_numpy(cons).cuda(), torch.from_numpy(bface).cuda()
+    sampler = ClockSampler(0)
+    s32, ms32, nsw, swms, launches, clocks = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP32_BULK,
+                                                       args.steps, args.warmup, None, sampler, None,
+                                                       variant=w5.W5CT_WENO_JS, floors=1)
+    hits, bad = s32.status()
+    divb32 = s32.div_b_norm()[0]
+    s32.close()
+    # error statement: FP64 and FP32-bulk from the same input at the same dt sequence
+    ne = args.err_steps
+    dts = torch.zeros(ne, dtype=torch.float64, device="cuda")
+    cfg64 = w5.make_config(precision=w5.W5CT_FP64, weno_variant=w5.W5CT_WENO_JS, floors=1)
+    g = w5.Solver(shape, dx, cfg64, stream=torch.cuda.current_stream().cuda_stream)
+    g.set_state(cons_d, bface_d)
+    t0 = time.perf_counter()
+    for k in range(ne):
+        g.step_cfl(dts[k:k + 1])
+    g.synchronize()
+    ms64 = 1e3 * (time.perf_counter() - t0) / ne
+    c64, b64, _ = g.get_state()
+    g.close()
+    cfg32 = w5.make_config(precision=w5.W5CT_FP32_BULK, weno_variant=w5.W5CT_WENO_JS, floors=1)
+    f = w5.Solver(shape, dx, cfg32, stream=torch.cuda.current_stream().cuda_stream)
+    f.set_state(cons_d, bface_d)
+    for k in range(ne):
+        w5.w5ct_step_dev(f.ctx, dts[k:k + 1])
+    c32, b32, _ = f.get_state()
+    f.close()
+    value = zones * args.steps / (ms32 * 1e-3)
+    ach = SWEEP_FLOPS_PER_ZONE * zones / (swms / nsw * 1e-3) / 1e12
+    line = {
+        "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value, "unit": "zone-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "accumulate": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"periodic {n}^3 magnetised blast (P 0.1 -> 100 inside r < 0.05, B = (1,1,1)/sqrt3, "
+                               f"beta 0.2) in k^-5/3 turbulence at rms Mach 5 (seed 1815); WENO-JS, CFL 0.8, "
+                               f"floors rho, P >= 1e-8", "zones": zones, "grid": [n, n, n],
+                   "l2_policy": "state larger than L2, no flush"},
+        "roofline": {"kernel": "sweep_kernel (FP32)", "bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / PEAK_FP32_TFLOPS, "traffic": sweep_traffic("fp32", zones),
+                     "launch_ms": swms / nsw},
+        "floor_hits": hits, "nonphysical": bad, "div_b_linf": divb32,
+        "fp64": {"ms_per_step": ms64, "value": zones / (ms64 * 1e-3), "error_steps": ne,
+                 "l1_fp32_vs_fp64": l1_error(c32, b32, c64, b64), "l1_fp64_change": l1_error(c64, b64, cons, bface),
+                 "max_rel_fp32_vs_fp64": float(max(np.abs(c32 - c64).max(), np.abs(b32 - b64).max()) /
+                                               max(np.abs(c64).max(), np.abs(b64).max()))},
+        "gpu_launches": launches, "clocks": clocks, "kernel_src": kernel_source_hash(),
+    }
+    print(json.dumps(line))
+
+
+def run_wave(args):
+    """The 32^3 fast magnetosonic eigenmode (amplitude 1e-6 along (1,2,2)/3),
+    FP64, WENO-Z, CFL 0.8: GPU steps and the oracle's steps on the host."""
+    import torch
+    torch.cuda.set_device(0)
+    import oracle
+    from paper_1812_04278_gb300 import build, inputs
+    build.build()
+    oracle.build()
+    from paper_1812_04278_gb300 import w5ct as w5
+    n = args.n
+    shape, zones = (n, n, n), n ** 3
+    cons, bface = inputs.fast_wave_config(shape)
+    s, ms, nsw, swms, launches, clocks = timed_run(torch, w5, shape, (1.0 / n,) * 3, torch.from_numpy(cons).cuda(),
+                                                   torch.from_numpy(bface).cuda(), w5.W5CT_FP64, args.steps,
+                                                   args.warmup, None, ClockSampler(0), None)
+    s.close()
+    o = oracle.Oracle(shape, 1.0 / n, oracle.make_config(weno_variant=oracle.WENO_Z))
+    o.set_state(cons, bface)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(o.cfl_dt())
+    el = time.perf_counter() - t0
+    value = zones * args.steps / (ms * 1e-3)
+    line = {
+        "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value, "unit": "zone-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"periodic {n}^3 fast magnetosonic eigenmode, amplitude 1e-6 along (1,2,2)/3, "
+                               f"rho=1, P=1, B=(1,sqrt2,1/2) in the wave frame; WENO-Z, CFL 0.8",
+                   "zones": zones, "grid": [n, n, n], "l2_policy": "state fits in L2 (launch-bound size)"},
+        "sweep_launch_ms": swms / nsw, "gpu_launches": launches, "clocks": clocks,
+        "cpu_baseline": {"value": zones * args.steps / el, "unit": "zone-updates/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": f"the same {args.steps} steps of the same {n}^3 input",
+                         "seconds": el},
+    }
+    print(json.dumps(line))
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "blast":
+        run_blast(args)
+    elif args.workload == "wave":
+        run_wave(args)
     else:
         run_native(args)
 

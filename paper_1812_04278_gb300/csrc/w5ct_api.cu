@@ -34,6 +34,7 @@ struct w5ct_ctx {
     double *oacc = nullptr;          // 3 planes
     // arithmetic-type buffers (float or double)
     void *qs = nullptr, *bs = nullptr, *bc = nullptr;        // 5, 3, 3 planes
+    void *q0r = nullptr, *b0r = nullptr;                     // q^n, b^n in float (aliases q0, b0 in FP64)
     void *Fx = nullptr, *Fy = nullptr, *Fz = nullptr;        // 5 planes each
     void *Sx = nullptr, *Sy = nullptr, *Sz = nullptr;        // 2 planes each
     // small device scalars
@@ -179,6 +180,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
         u.q0[f] = c->q0 + (size_t)f * n;
         u.acc[f] = c->acc + (size_t)f * n;
         u.qs[f] = plane<Real>(c->qs, n, f);
+        u.q0r[f] = plane<Real>(c->q0r, n, f);
     }
     for (int f = 0; f < 2; ++f) {
         u.Sx[f] = plane<Real>(c->Sx, n, f);
@@ -189,6 +191,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
         u.b0[f] = c->b0 + (size_t)f * n;
         u.oacc[f] = c->oacc + (size_t)f * n;
         u.bs[f] = plane<Real>(c->bs, n, f);
+        u.b0r[f] = plane<Real>(c->b0r, n, f);
     }
     u.dt = dt_dev;
 
@@ -339,6 +342,8 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     const size_t o_qs = take(5 * n * rs), o_bs = take(3 * n * rs), o_bc = take(3 * n * rs);
     const size_t o_Fx = take(5 * n * rs), o_Fy = take(5 * n * rs), o_Fz = take(5 * n * rs);
     const size_t o_Sx = take(2 * n * rs), o_Sy = take(2 * n * rs), o_Sz = take(2 * n * rs);
+    const bool fp32 = c->cfg.precision != W5CT_FP64;
+    const size_t o_q0r = fp32 ? take(5 * n * rs) : 0, o_b0r = fp32 ? take(3 * n * rs) : 0;
     const size_t o_dt = take(8), o_smax = take(24), o_flag = take(4), o_hits = take(8);
     const size_t o_part = take((size_t)kRedBlocks * 8 * 8), o_red = take(64), o_pl = take(64);
     void *slab = nullptr;
@@ -359,6 +364,8 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     c->Sx = b + o_Sx;
     c->Sy = b + o_Sy;
     c->Sz = b + o_Sz;
+    c->q0r = fp32 ? (void *)(b + o_q0r) : (void *)c->q0;
+    c->b0r = fp32 ? (void *)(b + o_b0r) : (void *)c->b0;
     c->dt_dev = (double *)(b + o_dt);
     c->smax = (unsigned long long *)(b + o_smax);
     c->flag = (int *)(b + o_flag);
@@ -392,6 +399,8 @@ int w5ct_set_state(w5ct_ctx *c, int patch, const double *cons, const double *bfa
         to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)(3 * n), c->b0, (float *)c->bs);
         c->launches += 2;
         W5_CUDA(c, cudaGetLastError());
+        W5_CUDA(c, cudaMemcpyAsync(c->q0r, c->qs, 5 * n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        W5_CUDA(c, cudaMemcpyAsync(c->b0r, c->bs, 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     }
     W5_CUDA(c, cudaMemsetAsync(c->flag, 0, 4, c->stream));
     W5_CUDA(c, cudaMemsetAsync(c->hits, 0, 8, c->stream));

@@ -147,6 +147,9 @@ struct UpdateArgs {
     const Real *Sx[2], *Sy[2], *Sz[2];
     double *q0[5], *acc[5], *b0[3], *oacc[3];
     Real *qs[5], *bs[3];
+    // q^n, b^n in the arithmetic type: the double arrays themselves when
+    // Real = double, a float copy written at the last stage when Real = float
+    Real *q0r[5], *b0r[3];
     const double *dt;
 };
 
@@ -159,8 +162,12 @@ struct StageW {
     static constexpr double wc = (S == 0 || S == 3) ? 1.0 / 6.0 : 1.0 / 3.0;
 };
 
+#ifndef W5CT_UPD_MINB
+#define W5CT_UPD_MINB 1
+#endif
+
 template <typename Real, int STAGE>
-__global__ void __launch_bounds__(256) update_kernel(UpdateArgs<Real> a) {
+__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<Real> a) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
@@ -174,24 +181,18 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs<Real> a) {
     const double dt = *a.dt;
     constexpr double c = StageW<STAGE>::c, wc = StageW<STAGE>::wc;
 
-    // ---- conserved fields
+    // Every load of this thread is issued before its first store, so that
+    // they can all be in flight together (the compiler cannot move a load
+    // above a store to a buffer that might alias it).
+
+    // ---- flux divergence (Eq. num) of the five conserved fields
+    Real D[5];
     {
         const size_t pxm = I(im, j, k), pym = I(i, jm, k), pzm = I(i, j, km);
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-            const Real D = (a.Fx[f][pxm] - a.Fx[f][p]) * a.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * a.rdy +
-                           (a.Fz[f][pzm] - a.Fz[f][p]) * a.rdz;
-            const double d = (double)D;
-            const double q0 = a.q0[f][p];
-            if (STAGE < 3) {
-                a.qs[f][p] = (Real)(q0 + (c * dt) * d);
-                a.acc[f][p] = (STAGE == 0 ? 0.0 : a.acc[f][p]) + wc * d;
-            } else {
-                const double qn = q0 + dt * (a.acc[f][p] + wc * d);
-                a.q0[f][p] = qn;
-                a.qs[f][p] = (Real)qn;
-            }
-        }
+        for (int f = 0; f < 5; ++f)
+            D[f] = (a.Fx[f][pxm] - a.Fx[f][p]) * a.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * a.rdy +
+                   (a.Fz[f][pzm] - a.Fz[f][p]) * a.rdz;
     }
 
     // ---- corner EMFs (Eqs. ox1-ox3) from the transport fluxes
@@ -219,19 +220,46 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs<Real> a) {
     const Real oz_km = Oz(i, ip, j, km, k);         // Omega_z(i, j, k-1)
     const Real oz_im = Oz(im, i, j, k, kp);         // Omega_z(i-1, j, k)
 
+    // ---- accumulators of this cell
+    double accv[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) accv[f] = STAGE == 0 ? 0.0 : a.acc[f][p];
+
     if (STAGE < 3) {
-        // face equations of Sec. 2.3 with this stage's EMFs
+        // The stage state is of the arithmetic type, so it is formed in that
+        // type from q^n, b^n (identical to the double expression when Real is
+        // double); the accumulators stay in double.
+        Real q0v[5], b0v[3];
+        double oav[3];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) q0v[f] = a.q0r[f][p];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            b0v[f] = a.b0r[f][p];
+            oav[f] = STAGE == 0 ? 0.0 : a.oacc[f][p];
+        }
+        // RK stage (Sec. 2.1) and face equations of Sec. 2.3 with this stage's EMFs
         const Real dbx = -(ox_c - ox_jm) * a.rdy + (oz_c - oz_km) * a.rdz;
         const Real dby = -(oy_c - oy_km) * a.rdz + (ox_c - ox_im) * a.rdx;
         const Real dbz = -(oz_c - oz_im) * a.rdx + (oy_c - oy_jm) * a.rdy;
-        const double cdt = c * dt;
-        a.bs[0][p] = (Real)(a.b0[0][p] + cdt * (double)dbx);
-        a.bs[1][p] = (Real)(a.b0[1][p] + cdt * (double)dby);
-        a.bs[2][p] = (Real)(a.b0[2][p] + cdt * (double)dbz);
-        a.oacc[0][p] = (STAGE == 0 ? 0.0 : a.oacc[0][p]) + wc * (double)ox_c;
-        a.oacc[1][p] = (STAGE == 0 ? 0.0 : a.oacc[1][p]) + wc * (double)oy_c;
-        a.oacc[2][p] = (STAGE == 0 ? 0.0 : a.oacc[2][p]) + wc * (double)oz_c;
+        const Real cdt = (Real)(c * dt);
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            a.qs[f][p] = q0v[f] + cdt * D[f];
+            a.acc[f][p] = accv[f] + wc * (double)D[f];
+        }
+        a.bs[0][p] = b0v[0] + cdt * dbx;
+        a.bs[1][p] = b0v[1] + cdt * dby;
+        a.bs[2][p] = b0v[2] + cdt * dbz;
+        a.oacc[0][p] = oav[0] + wc * (double)ox_c;
+        a.oacc[1][p] = oav[1] + wc * (double)oy_c;
+        a.oacc[2][p] = oav[2] + wc * (double)oz_c;
     } else {
+        double q0v[5], b0v[3];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) q0v[f] = a.q0[f][p];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) b0v[f] = a.b0[f][p];
         // accumulated EMFs sum_k w'_k Omega_k, in double, at the nine edges
         const double *Ax = a.oacc[0], *Ay = a.oacc[1], *Az = a.oacc[2];
         const double ax_c = Ax[p] + wc * (double)ox_c;
@@ -246,15 +274,22 @@ __global__ void __launch_bounds__(256) update_kernel(UpdateArgs<Real> a) {
         const double dbx = -(ax_c - ax_jm) * a.drdy + (az_c - az_km) * a.drdz;
         const double dby = -(ay_c - ay_km) * a.drdz + (ax_c - ax_im) * a.drdx;
         const double dbz = -(az_c - az_im) * a.drdx + (ay_c - ay_jm) * a.drdy;
-        const double bxn = a.b0[0][p] + dt * dbx;
-        const double byn = a.b0[1][p] + dt * dby;
-        const double bzn = a.b0[2][p] + dt * dbz;
-        a.b0[0][p] = bxn;
-        a.b0[1][p] = byn;
-        a.b0[2][p] = bzn;
-        a.bs[0][p] = (Real)bxn;
-        a.bs[1][p] = (Real)byn;
-        a.bs[2][p] = (Real)bzn;
+        // last stage: q^{n+1} = q0 + dt sum_k w_k c_k D_k and the final CT update
+        constexpr bool kCopy = !std::is_same<Real, double>::value;   // float copy of q^{n+1}, b^{n+1}
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            const double qn = q0v[f] + dt * (accv[f] + wc * (double)D[f]);
+            a.q0[f][p] = qn;
+            a.qs[f][p] = (Real)qn;
+            if (kCopy) a.q0r[f][p] = (Real)qn;
+        }
+        const double bn[3] = {b0v[0] + dt * dbx, b0v[1] + dt * dby, b0v[2] + dt * dbz};
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            a.b0[f][p] = bn[f];
+            a.bs[f][p] = (Real)bn[f];
+            if (kCopy) a.b0r[f][p] = (Real)bn[f];
+        }
     }
 }
 

@@ -242,27 +242,32 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
 
 // Eq. (FWENO) for one characteristic field from its 11 projections:
 // P[0] = L.central, P[1..5] = L.dF at i-3/2 .. i+5/2, P[6..10] = L.du there.
+//
+// The split differences are (dF +- alpha dq)/2.  IS_k scales with the square
+// of its arguments and phi_N linearly, so phi_N(x/2; eps) = phi_N(x; 4 eps)/2
+// for both weight variants: the factor 1/2 is applied once to the result and
+// eps4 = 4 eps is passed in.
 template <typename Real, int VAR>
-__device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps) {
-    const Real ha = Real(0.5) * alpha;
+__device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps4) {
     Real p[5], q[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        p[j] = Real(0.5) * P[1 + j] + ha * P[6 + j];
-        q[j] = Real(0.5) * P[1 + j] - ha * P[6 + j];
+        p[j] = P[1 + j] + alpha * P[6 + j];
+        q[j] = P[1 + j] - alpha * P[6 + j];
     }
     if constexpr (std::is_same<Real, double>::value) {
         double Np, Dp, Nm, Dm;
-        phi_nd<VAR>(p[0], p[1], p[2], p[3], eps, Np, Dp);
-        phi_nd<VAR>(q[4], q[3], q[2], q[1], eps, Nm, Dm);
+        phi_nd<VAR>(p[0], p[1], p[2], p[3], eps4, Np, Dp);
+        phi_nd<VAR>(q[4], q[3], q[2], q[1], eps4, Nm, Dm);
         const double prod = Dp * Dm;
         if (prod > 1e-290 && prod < 1e290) {
             // -Np/Dp + Nm/Dm over the common denominator: one division
-            return P[0] + (Nm * Dp - Np * Dm) / prod;
+            return P[0] + 0.5 * ((Nm * Dp - Np * Dm) / prod);
         }
-        return P[0] - Np / Dp + Nm / Dm;
+        return P[0] + 0.5 * (Nm / Dm - Np / Dp);
     } else {
-        return P[0] - phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps) + phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps);
+        return P[0] + Real(0.5) * (phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps4) -
+                                   phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps4));
     }
 }
 
@@ -397,7 +402,7 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     const Real ics2 = m::rcp_(cs2);
     const Real pre = Real(0.5) * ics2;
     const Real tau = K.gm1 * ics2;
-    const Real eps = K.eps_w;
+    const Real eps = Real(4) * K.eps_w;   // see weno_field
 
     // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
     {

@@ -314,3 +314,55 @@ def random_smooth_state(shape, seed, mach=0.5, beta=1.0, dB_frac=0.3, drho=0.2, 
     P = (1.0 / gamma) * (1.0 + drho * np.cos(2 * np.pi * (X + Y) + a[3]) + 0.5 * drho * np.sin(2 * np.pi * Z + a[4]))
     v = cons[1:4] / cons[0]
     return assemble(rho, v, P, bface, gamma)
+
+
+def analytic_smooth_state(shape, seed=0, amp=0.2, gamma=GAMMA, dtype=np.float64):
+    """Large smooth state without FFTs (for grids where spectral synthesis is
+    too slow): a few separable sine modes in rho, v and P and an edge vector
+    potential A_i = a sin(2 pi (k.x) + phi) sampled at the edges, plus a
+    uniform mean field.  All fields O(1); div b = 0 to rounding."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    ph = rng.uniform(0, 2 * np.pi, 16)
+    hx, hy, hz = 1.0 / nx, 1.0 / ny, 1.0 / nz
+    x = ((np.arange(nx) + 0.5) * hx)[None, None, :]
+    y = ((np.arange(ny) + 0.5) * hy)[None, :, None]
+    z = ((np.arange(nz) + 0.5) * hz)[:, None, None]
+    tp = 2 * np.pi
+    rho = 1.0 + amp * np.sin(tp * x + ph[0]) * np.cos(tp * y + ph[1]) + 0.5 * amp * np.sin(tp * z + ph[2])
+    P = (1.0 / gamma) * (1.0 + amp * np.cos(tp * y + ph[3]) * np.sin(tp * z + ph[4]) + 0.5 * amp * np.cos(tp * x + ph[5]))
+    v = np.empty((3, nz, ny, nx), dtype=np.float64)
+    v[0] = 0.5 * np.sin(tp * y + ph[6]) + 0.3 * np.cos(tp * z + ph[7]) + 0 * x
+    v[1] = 0.5 * np.sin(tp * z + ph[8]) + 0.3 * np.cos(tp * x + ph[9]) + 0 * y
+    v[2] = 0.5 * np.sin(tp * x + ph[10]) + 0.3 * np.cos(tp * y + ph[11]) + 0 * z
+    a = 0.3 / tp
+    # edges: Ax (i, j+1/2, k+1/2), Ay (i+1/2, j, k+1/2), Az (i+1/2, j+1/2, k)
+    Ax = a * np.sin(tp * (y + 0.5 * hy) + ph[12]) * np.cos(tp * (z + 0.5 * hz) + ph[13]) + 0 * x
+    Ay = a * np.sin(tp * (z + 0.5 * hz) + ph[14]) * np.cos(tp * (x + 0.5 * hx) + ph[15]) + 0 * y
+    Az = a * np.sin(tp * (x + 0.5 * hx) + ph[12]) * np.cos(tp * (y + 0.5 * hy) + ph[14]) + 0 * z
+    bx, by, bz = curl_edges_to_faces(Ax, Ay, Az, (hx, hy, hz))
+    bface = np.stack([bx + 0.8, by + 0.4, bz - 0.5])
+    del Ax, Ay, Az, bx, by, bz
+    cons, bface = assemble(rho, v, P, bface, gamma)
+    return cons.astype(dtype, copy=False), bface.astype(dtype, copy=False)
+
+
+def blast_turbulence_state(N, seed=1815, seed_b=1816, mach=5.0, p_amb=0.1, p_blast=100.0, r_blast=0.05,
+                           dB_frac=0.1, kmin=2, kmax=32, gamma=GAMMA):
+    """Magnetised blast in a turbulent background (the paper's blast test,
+    Sec. 4.16, in a turbulent medium): rho = 1, ambient P = p_amb, uniform
+    field B = (1, 1, 1)/sqrt3 (beta = 2 p_amb / |B|^2), solenoidal k^-5/3
+    velocity at rms Mach `mach` with respect to the ambient sound speed, a
+    10% rms field perturbation, and P = p_blast inside r < r_blast of the
+    box centre (top hat at cell centres)."""
+    shape = (N, N, N)
+    B0 = 1.0
+    beta = 2.0 * p_amb / B0 ** 2
+    cons, bface = turbulent_state(N, seed=seed, seed_b=seed_b, mach=mach, beta=beta, dB_frac=dB_frac, kmin=kmin,
+                                  kmax=min(kmax, N // 2 - 1), gamma=gamma, B_dir=(1.0, 1.0, 1.0), P0=p_amb)
+    X, Y, Z, _ = cell_centres(shape)
+    r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+    inside = r2 < r_blast ** 2
+    # raise the pressure inside the sphere: E grows by (p_blast - p_amb)/(gamma - 1)
+    cons[4] += np.where(inside, (p_blast - p_amb) / (gamma - 1.0), 0.0)
+    return cons, bface
