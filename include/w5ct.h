@@ -3,7 +3,8 @@
  * fifth-order finite-difference WENO + constrained-transport ideal-MHD
  * scheme of Donnert et al., "WENO-Wombat" (arXiv:1812.04278).
  *
- * One context advances one periodic patch with the paper's scheme:
+ * One context advances one or more independent periodic patches with the
+ * paper's scheme:
  *   - the per-axis characteristic flux update (Sec. 2.2, Eq. FWENO, with
  *     the eigenvectors of Appendix A and local Lax-Friedrichs splitting),
  *   - the Ryu et al. transport-flux CT update of the face fields
@@ -92,13 +93,17 @@ int w5ct_destroy(w5ct_ctx *ctx);
 /* Replace the stream all later device work is enqueued on. */
 int w5ct_set_stream(w5ct_ctx *ctx, void *stream);
 
-/* Allocate one periodic patch (the paper's patch, Sec. 3).  npatch must be
- * 1 (W5CT_ERR_UNSUPPORTED otherwise); n3 = {nx, ny, nz}, each >= 1;
- * dx3 = {dx, dy, dz} > 0 (host pointers).  Previous buffers are freed. */
+/* Allocate npatch >= 1 independent periodic patches (the paper's patches,
+ * Sec. 3; here each is its own periodic box, with no exchange between them).
+ * n3 = {nx, ny, nz} per patch (npatch x 3 ints, each >= 1) and dx3 = {dx, dy,
+ * dz} per patch (npatch x 3 doubles > 0), host pointers.  With npatch > 1
+ * every step advances all patches together, each kernel launch covering the
+ * tiles of every patch.  Previous buffers are freed. */
 int w5ct_init_grid(w5ct_ctx *ctx, int npatch, const int *n3, const double *dx3);
 
-/* Load the state q^n: cons (5 planes) and bface (3 planes), host or device
- * (on_device).  patch must be 0.  The face field should be discretely
+/* Load the state q^n of patch `patch` (0 .. npatch-1): cons (5 planes) and
+ * bface (3 planes) of that patch's size, host or device (on_device).  Every
+ * patch needs a state before the first step.  The face field should be discretely
  * divergence-free; the scheme keeps its divergence at round-off (Sec. 2.3)
  * but does not remove an initial one. */
 int w5ct_set_state(w5ct_ctx *ctx, int patch, const double *cons, const double *bface, int on_device);
@@ -108,38 +113,45 @@ int w5ct_set_state(w5ct_ctx *ctx, int patch, const double *cons, const double *b
  * non-physical state (the buffers are still written). */
 int w5ct_get_state(w5ct_ctx *ctx, int patch, double *cons, double *bface, double *bcell, int on_device);
 
-/* One full RK4 + CT step of size dt > 0 (Secs. 2.1, 2.3, 3.1.3): four
- * stages of x-, y- and z-sweeps of the characteristic WENO flux, the
- * transport-flux corrections and corner EMFs, the face-field update and
- * the fourth-order face-to-centre interpolation.  Asynchronous. */
+/* One full RK4 + CT step of size dt > 0 (Secs. 2.1, 2.3, 3.1.3) of every
+ * patch: four stages of x-, y- and z-sweeps of the characteristic WENO
+ * flux, the transport-flux corrections and corner EMFs, the face-field
+ * update and the fourth-order face-to-centre interpolation.  Asynchronous. */
 int w5ct_step(w5ct_ctx *ctx, double dt);
 
-/* As w5ct_step with dt read from device memory at *dt_dev (one double,
- * read by the kernels when they run), so a sequence of steps can be
- * captured in a CUDA graph. */
+/* As w5ct_step with the dt of patch p read from device memory at dt_dev[p]
+ * (npatch doubles, read by the kernels when they run), so a sequence of
+ * steps can be captured in a CUDA graph. */
 int w5ct_step_dev(w5ct_ctx *ctx, const double *dt_dev);
 
-/* One step with dt = CFL / sum_d (S_d / dx_d) computed on the device from
- * the current state (Eq. cfl, with S_d from w5ct_max_signal_speed); no
- * host synchronisation.  If dt_dev_out is not NULL the dt used is also
- * written there (device pointer, one double). */
+/* One step in which every patch takes its own dt = CFL / sum_d (S_d / dx_d),
+ * computed on the device from its current state (Eq. cfl, with S_d from
+ * w5ct_max_signal_speed); no host synchronisation.  If dt_dev_out is not
+ * NULL the dts used are also written there (device pointer, npatch doubles). */
 int w5ct_step_cfl(w5ct_ctx *ctx, double *dt_dev_out);
 
-/* S_d = max over cells of |v_d| + c_fast^d for d = x, y, z (Eq. cfl; the
+/* nsteps >= 0 steps as w5ct_step_cfl(ctx, NULL), replayed from a CUDA graph
+ * of one step that the first call captures (on a private stream) and later
+ * calls reuse; the graph is launched on the context's stream.  The graph is
+ * dropped by w5ct_init_grid and w5ct_destroy.  Asynchronous. */
+int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
+
+/* For patch `patch`: S_d = max over its cells of |v_d| + c_fast^d for d = x, y, z (Eq. cfl; the
  * fast speed of Eq. fast with B_n = B_d), out[3] on the host.  Synchronises.
  * FP32_BULK evaluates the speeds in float. */
 int w5ct_max_signal_speed(w5ct_ctx *ctx, int patch, double out[3]);
 
-/* dt = CFL / sum_d (S_d / dx_d) on the host.  Synchronises. */
+/* dt = CFL / sum_d (S_d / dx_d) on the host, the smallest over the
+ * patches (the common dt of a lockstep advance).  Synchronises. */
 int w5ct_cfl_dt(w5ct_ctx *ctx, double *dt);
 
-/* Discrete divergence of the face field at cell centres,
+/* Discrete divergence of the face field of patch `patch` at cell centres,
  * (b_x(i) - b_x(i-1))/dx + (b_y(j) - b_y(j-1))/dy + (b_z(k) - b_z(k-1))/dz:
  * *linf its maximum modulus, *l2 its root mean square.  FP64, deterministic.
  * Synchronises. */
 int w5ct_div_b_norm(w5ct_ctx *ctx, int patch, double *linf, double *l2);
 
-/* Volume integrals (sum * dx*dy*dz) of rho, m_x, m_y, m_z, E, b_x, b_y, b_z
+/* Volume integrals over patch `patch` (sum * dx*dy*dz) of rho, m_x, m_y, m_z, E, b_x, b_y, b_z
  * in out[8] (host).  FP64, fixed summation order (deterministic).
  * Synchronises. */
 int w5ct_conserved_totals(w5ct_ctx *ctx, int patch, double out[8]);

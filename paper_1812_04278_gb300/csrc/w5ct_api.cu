@@ -45,6 +45,18 @@ struct w5ct_ctx {
     double *part = nullptr;          // kRedBlocks x 8
     double *red_out = nullptr;       // 8
     const double **planes = nullptr; // 8 device pointers
+    // several patches (npatch > 1): planes hold the patches back to back
+    int npatch = 0;
+    std::vector<PatchGeom> pg;       // host copy of the patch table
+    PatchGeom *pg_dev = nullptr;     // device patch table
+    int4 *tiles_dev[3] = {nullptr, nullptr, nullptr};   // sweep tiles per axis
+    int ntiles[3] = {0, 0, 0};
+    int4 *cells_dev = nullptr;       // 32 x 8 cell blocks of every patch
+    int ncells = 0;
+    // captured step (w5ct_step_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;
     // timing and accounting
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -100,11 +112,19 @@ Real *plane(void *base, long long n, int f) {
 }
 
 void free_grid(w5ct_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->graph_kernels = 0;
     if (c->slab) cudaFree(c->slab);
     c->slab = nullptr;
     c->have_grid = false;
     c->have_state = false;
+    c->npatch = 0;
+    c->pg.clear();
 }
+
+// geometry of patch p as the single-patch kernels see it
+PatchGeom patch_of(const w5ct_ctx *c, int p) { return c->pg[p]; }
 
 dim3 cell_grid(const w5ct_ctx *c) { return dim3((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz); }
 
@@ -122,24 +142,51 @@ int record_event(w5ct_ctx *c) {
 template <typename Real>
 int launch_cellb(w5ct_ctx *c) {
     const long long n = c->n;
-    cellb_kernel<Real><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(
-        c->nx, c->ny, c->nz, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
-        plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
+    if (c->npatch > 1) {
+        cellb_batched_kernel<Real><<<c->ncells, dim3(32, 8), 0, c->stream>>>(
+            c->pg_dev, c->cells_dev, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
+            plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
+    } else {
+        cellb_kernel<Real><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(
+            c->nx, c->ny, c->nz, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
+            plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
+    }
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
     return W5CT_OK;
 }
 
+// maxima S_d of every patch into smax[3 p + d]
 template <typename Real>
 int launch_speed(w5ct_ctx *c) {
     const long long n = c->n;
-    W5_CUDA(c, cudaMemsetAsync(c->smax, 0, 3 * sizeof(unsigned long long), c->stream));
-    long long nb = (n + kRedThreads - 1) / kRedThreads;
-    if (nb > 4 * 152) nb = 4 * 152;
-    speed_kernel<Real><<<(unsigned)nb, kRedThreads, 0, c->stream>>>(
-        n, c->nx, c->ny, plane<Real>(c->qs, n, 0), plane<Real>(c->qs, n, 1), plane<Real>(c->qs, n, 2),
-        plane<Real>(c->qs, n, 3), plane<Real>(c->qs, n, 4), plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1),
-        plane<Real>(c->bc, n, 2), make_phys<Real>(c->cfg), c->smax, c->flag);
+    W5_CUDA(c, cudaMemsetAsync(c->smax, 0, 3 * sizeof(unsigned long long) * (size_t)c->npatch, c->stream));
+    if (c->npatch > 1) {
+        speed_batched_kernel<Real><<<c->ncells, dim3(32, 8), 0, c->stream>>>(
+            c->pg_dev, c->cells_dev, plane<Real>(c->qs, n, 0), plane<Real>(c->qs, n, 1), plane<Real>(c->qs, n, 2),
+            plane<Real>(c->qs, n, 3), plane<Real>(c->qs, n, 4), plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1),
+            plane<Real>(c->bc, n, 2), make_phys<Real>(c->cfg), c->smax, c->flag);
+    } else {
+        long long nb = (n + kRedThreads - 1) / kRedThreads;
+        if (nb > 4 * 152) nb = 4 * 152;
+        speed_kernel<Real><<<(unsigned)nb, kRedThreads, 0, c->stream>>>(
+            n, c->nx, c->ny, plane<Real>(c->qs, n, 0), plane<Real>(c->qs, n, 1), plane<Real>(c->qs, n, 2),
+            plane<Real>(c->qs, n, 3), plane<Real>(c->qs, n, 4), plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1),
+            plane<Real>(c->bc, n, 2), make_phys<Real>(c->cfg), c->smax, c->flag);
+    }
+    c->launches++;
+    W5_CUDA(c, cudaGetLastError());
+    return W5CT_OK;
+}
+
+// dt of every patch from the maxima (one launch)
+int launch_dt(w5ct_ctx *c, double *dt_copy) {
+    if (c->npatch > 1) {
+        dt_batched_kernel<<<(c->npatch + 127) / 128, 128, 0, c->stream>>>(c->pg_dev, c->npatch, c->smax, c->cfg.cfl,
+                                                                        c->dt_dev, dt_copy);
+    } else {
+        dt_kernel<<<1, 1, 0, c->stream>>>(c->smax, c->cfg.cfl, c->dx, c->dy, c->dz, c->dt_dev, dt_copy);
+    }
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
     return W5CT_OK;
@@ -147,7 +194,10 @@ int launch_speed(w5ct_ctx *c) {
 
 template <typename Real, int S>
 void launch_update_stage(w5ct_ctx *c, const UpdateArgs<Real> &u) {
-    update_kernel<Real, S><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(u);
+    if (c->npatch > 1)
+        update_batched_kernel<Real, S><<<c->ncells, dim3(32, 8), 0, c->stream>>>(u, c->pg_dev, c->cells_dev, u.dt);
+    else
+        update_kernel<Real, S><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(u);
 }
 
 template <typename Real>
@@ -208,7 +258,11 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
             for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
             int rc = record_event(c);
             if (rc) return rc;
-            W5_CUDA(c, launch_sweep<Real>(ax, variant, a, c->stream));
+            if (c->npatch > 1)
+                W5_CUDA(c, launch_sweep_batched<Real>(ax, variant, a, c->pg_dev, c->tiles_dev[ax], c->ntiles[ax],
+                                                      c->stream));
+            else
+                W5_CUDA(c, launch_sweep<Real>(ax, variant, a, c->stream));
             c->launches++;
             rc = record_event(c);
             if (rc) return rc;
@@ -245,18 +299,25 @@ int read_flag(w5ct_ctx *c, int *flag_out) {
     return W5CT_OK;
 }
 
-int speeds_impl(w5ct_ctx *c, double out[3]) {
+// S_d of every patch into out[3 p + d] (host, 3 * npatch doubles)
+int speeds_impl(w5ct_ctx *c, double *out) {
     int rc = c->cfg.precision == W5CT_FP64 ? launch_cellb<double>(c) : launch_cellb<float>(c);
     if (rc) return rc;
     rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
     if (rc) return rc;
-    unsigned long long bits[3];
-    W5_CUDA(c, cudaMemcpyAsync(bits, c->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned long long> bits(3 * (size_t)c->npatch);
+    W5_CUDA(c, cudaMemcpyAsync(bits.data(), c->smax, bits.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
     int flag = 0;
     rc = read_flag(c, &flag);
     if (rc) return rc;
-    for (int d = 0; d < 3; ++d) memcpy(&out[d], &bits[d], sizeof(double));
+    for (size_t d = 0; d < bits.size(); ++d) memcpy(&out[d], &bits[d], sizeof(double));
     if (flag) return fail(c, W5CT_ERR_NONPHYSICAL, "non-physical state (rho <= 0, P <= 0 or NaN)");
+    return W5CT_OK;
+}
+
+int check_patch(w5ct_ctx *c, int patch) {
+    if (patch < 0 || patch >= c->npatch) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
     return W5CT_OK;
 }
 
@@ -307,6 +368,7 @@ int w5ct_destroy(w5ct_ctx *c) {
     if (!c) return W5CT_OK;
     if (c->have_grid) cudaStreamSynchronize(c->stream);
     free_grid(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
     return W5CT_OK;
@@ -322,33 +384,88 @@ int w5ct_set_stream(w5ct_ctx *c, void *stream) {
 int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     if (!c) return W5CT_ERR_ARG;
     if (!n3 || !dx3) return fail(c, W5CT_ERR_ARG, "null n3 or dx3");
-    if (npatch != 1) return fail(c, W5CT_ERR_UNSUPPORTED, "only npatch = 1 is implemented (got %d)", npatch);
-    if (n3[0] < 1 || n3[1] < 1 || n3[2] < 1) return fail(c, W5CT_ERR_ARG, "grid sizes must be >= 1");
-    if (n3[0] > 65535 * 32 || n3[1] > 65535 * 8 || n3[2] > 65535)
-        return fail(c, W5CT_ERR_ARG, "grid too large for the launch geometry");
-    if (!(dx3[0] > 0) || !(dx3[1] > 0) || !(dx3[2] > 0)) return fail(c, W5CT_ERR_ARG, "spacings must be > 0");
+    if (npatch < 1 || npatch > (1 << 24)) return fail(c, W5CT_ERR_ARG, "npatch must be in 1 .. 2^24 (got %d)", npatch);
+    long long ntot = 0;
+    for (int p = 0; p < npatch; ++p) {
+        const int *m = n3 + 3 * p;
+        const double *h = dx3 + 3 * p;
+        if (m[0] < 1 || m[1] < 1 || m[2] < 1) return fail(c, W5CT_ERR_ARG, "patch %d: grid sizes must be >= 1", p);
+        if (m[0] > 65535 * 32 || m[1] > 65535 * 8 || m[2] > 65535)
+            return fail(c, W5CT_ERR_ARG, "patch %d: grid too large for the launch geometry", p);
+        if (!(h[0] > 0) || !(h[1] > 0) || !(h[2] > 0)) return fail(c, W5CT_ERR_ARG, "patch %d: spacings must be > 0", p);
+        ntot += (long long)m[0] * m[1] * m[2];
+    }
     free_grid(c);
+    c->npatch = npatch;
+    c->pg.resize(npatch);
+    long long off = 0;
+    for (int p = 0; p < npatch; ++p) {
+        PatchGeom &g = c->pg[p];
+        g.nx = n3[3 * p];
+        g.ny = n3[3 * p + 1];
+        g.nz = n3[3 * p + 2];
+        g.pad = 0;
+        g.off = off;
+        g.dx = dx3[3 * p];
+        g.dy = dx3[3 * p + 1];
+        g.dz = dx3[3 * p + 2];
+        g.rdx = 1.0 / g.dx;
+        g.rdy = 1.0 / g.dy;
+        g.rdz = 1.0 / g.dz;
+        off += (long long)g.nx * g.ny * g.nz;
+    }
     c->nx = n3[0];
     c->ny = n3[1];
     c->nz = n3[2];
-    c->n = (long long)c->nx * c->ny * c->nz;
+    c->n = ntot;
     c->dx = dx3[0];
     c->dy = dx3[1];
     c->dz = dx3[2];
+    // tile tables of the batched kernels: (patch, tile x, tile y, tile z)
+    std::vector<int4> tiles[3], cells;
+    if (npatch > 1) {
+        const int t2x = c->cfg.precision == W5CT_FP64 ? sweep_t2<double>(0) : sweep_t2<float>(0);
+        const int t2yz = c->cfg.precision == W5CT_FP64 ? sweep_t2<double>(1) : sweep_t2<float>(1);
+        for (int p = 0; p < npatch; ++p) {
+            const PatchGeom &g = c->pg[p];
+            const int bx = (g.nx + 31) / 32;
+            for (int k = 0; k < g.nz; ++k)
+                for (int j = 0; j < (g.ny + t2x - 1) / t2x; ++j)
+                    for (int i = 0; i < bx; ++i) tiles[0].push_back(make_int4(p, i, j, k));
+            for (int k = 0; k < g.nz; ++k)
+                for (int j = 0; j < (g.ny + t2yz - 1) / t2yz; ++j)
+                    for (int i = 0; i < bx; ++i) tiles[1].push_back(make_int4(p, i, j, k));
+            for (int k = 0; k < (g.nz + t2yz - 1) / t2yz; ++k)
+                for (int j = 0; j < g.ny; ++j)
+                    for (int i = 0; i < bx; ++i) tiles[2].push_back(make_int4(p, i, j, k));
+            for (int k = 0; k < g.nz; ++k)
+                for (int j = 0; j < (g.ny + 7) / 8; ++j)
+                    for (int i = 0; i < bx; ++i) cells.push_back(make_int4(p, i, j, k));
+        }
+        for (int a = 0; a < 3; ++a) c->ntiles[a] = (int)tiles[a].size();
+        c->ncells = (int)cells.size();
+    }
     const size_t n = (size_t)c->n, rs = c->real_size;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    size_t bytes_total = 0;
+    auto take = [&](size_t bytes) { size_t o = bytes_total; bytes_total += align256(bytes); return o; };
     const size_t o_q0 = take(5 * n * 8), o_b0 = take(3 * n * 8), o_acc = take(5 * n * 8), o_oacc = take(3 * n * 8);
     const size_t o_qs = take(5 * n * rs), o_bs = take(3 * n * rs), o_bc = take(3 * n * rs);
     const size_t o_Fx = take(5 * n * rs), o_Fy = take(5 * n * rs), o_Fz = take(5 * n * rs);
     const size_t o_Sx = take(2 * n * rs), o_Sy = take(2 * n * rs), o_Sz = take(2 * n * rs);
     const bool fp32 = c->cfg.precision != W5CT_FP64;
     const size_t o_q0r = fp32 ? take(5 * n * rs) : 0, o_b0r = fp32 ? take(3 * n * rs) : 0;
-    const size_t o_dt = take(8), o_smax = take(24), o_flag = take(4), o_hits = take(8);
+    const size_t np = (size_t)npatch;
+    const size_t o_dt = take(8 * np), o_smax = take(24 * np), o_flag = take(4), o_hits = take(8);
     const size_t o_part = take((size_t)kRedBlocks * 8 * 8), o_red = take(64), o_pl = take(64);
+    const size_t o_pg = take(sizeof(PatchGeom) * np);
+    size_t o_tiles[3] = {0, 0, 0}, o_cells = 0;
+    if (npatch > 1) {
+        for (int a = 0; a < 3; ++a) o_tiles[a] = take(sizeof(int4) * tiles[a].size());
+        o_cells = take(sizeof(int4) * cells.size());
+    }
     void *slab = nullptr;
-    cudaError_t e = cudaMalloc(&slab, off);
-    if (e != cudaSuccess) return fail(c, W5CT_ERR_CUDA, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
+    cudaError_t e = cudaMalloc(&slab, bytes_total);
+    if (e != cudaSuccess) return fail(c, W5CT_ERR_CUDA, "cudaMalloc(%zu bytes): %s", bytes_total, cudaGetErrorString(e));
     char *b = (char *)slab;
     c->slab = slab;
     c->q0 = (double *)(b + o_q0);
@@ -373,6 +490,18 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     c->part = (double *)(b + o_part);
     c->red_out = (double *)(b + o_red);
     c->planes = (const double **)(b + o_pl);
+    c->pg_dev = (PatchGeom *)(b + o_pg);
+    W5_CUDA(c, cudaMemcpy(c->pg_dev, c->pg.data(), sizeof(PatchGeom) * np, cudaMemcpyHostToDevice));
+    if (npatch > 1) {
+        for (int a = 0; a < 3; ++a) {
+            c->tiles_dev[a] = (int4 *)(b + o_tiles[a]);
+            W5_CUDA(c, cudaMemcpy(c->tiles_dev[a], tiles[a].data(), sizeof(int4) * tiles[a].size(),
+                                  cudaMemcpyHostToDevice));
+        }
+        c->cells_dev = (int4 *)(b + o_cells);
+        W5_CUDA(c, cudaMemcpy(c->cells_dev, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice));
+    }
+    W5_CUDA(c, c->cfg.precision == W5CT_FP64 ? prepare_sweeps<double>() : prepare_sweeps<float>());
     W5_CUDA(c, cudaMemsetAsync(c->flag, 0, 4, c->stream));
     W5_CUDA(c, cudaMemsetAsync(c->hits, 0, 8, c->stream));
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -383,24 +512,45 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
 int w5ct_set_state(w5ct_ctx *c, int patch, const double *cons, const double *bface, int on_device) {
     if (!c) return W5CT_ERR_ARG;
     if (!c->have_grid) return fail(c, W5CT_ERR_STATE, "no grid: call w5ct_init_grid first");
-    if (patch != 0) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
     if (!cons || !bface) return fail(c, W5CT_ERR_ARG, "null cons or bface");
     const size_t n = (size_t)c->n;
+    const PatchGeom g = patch_of(c, patch);
+    const size_t np = (size_t)g.nx * g.ny * g.nz, off = (size_t)g.off;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    W5_CUDA(c, cudaMemcpyAsync(c->q0, cons, 5 * n * sizeof(double), kind, c->stream));
-    W5_CUDA(c, cudaMemcpyAsync(c->b0, bface, 3 * n * sizeof(double), kind, c->stream));
-    if (c->cfg.precision == W5CT_FP64) {
-        W5_CUDA(c, cudaMemcpyAsync(c->qs, c->q0, 5 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
-        W5_CUDA(c, cudaMemcpyAsync(c->bs, c->b0, 3 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->npatch == 1) {
+        W5_CUDA(c, cudaMemcpyAsync(c->q0, cons, 5 * n * sizeof(double), kind, c->stream));
+        W5_CUDA(c, cudaMemcpyAsync(c->b0, bface, 3 * n * sizeof(double), kind, c->stream));
     } else {
-        long long nb = ((long long)5 * n + 255) / 256;
+        for (int f = 0; f < 5; ++f)
+            W5_CUDA(c, cudaMemcpyAsync(c->q0 + f * n + off, cons + f * np, np * sizeof(double), kind, c->stream));
+        for (int f = 0; f < 3; ++f)
+            W5_CUDA(c, cudaMemcpyAsync(c->b0 + f * n + off, bface + f * np, np * sizeof(double), kind, c->stream));
+    }
+    if (c->cfg.precision == W5CT_FP64) {
+        for (int f = 0; f < 5; ++f)
+            W5_CUDA(c, cudaMemcpyAsync((double *)c->qs + f * n + off, c->q0 + f * n + off, np * 8,
+                                       cudaMemcpyDeviceToDevice, c->stream));
+        for (int f = 0; f < 3; ++f)
+            W5_CUDA(c, cudaMemcpyAsync((double *)c->bs + f * n + off, c->b0 + f * n + off, np * 8,
+                                       cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        long long nb = ((long long)np + 255) / 256;
         if (nb > 8 * 152) nb = 8 * 152;
-        to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)(5 * n), c->q0, (float *)c->qs);
-        to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)(3 * n), c->b0, (float *)c->bs);
-        c->launches += 2;
+        for (int f = 0; f < 5; ++f) {
+            to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)np, c->q0 + f * n + off,
+                                                                      (float *)c->qs + f * n + off);
+            to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)np, c->q0 + f * n + off,
+                                                                      (float *)c->q0r + f * n + off);
+        }
+        for (int f = 0; f < 3; ++f) {
+            to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)np, c->b0 + f * n + off,
+                                                                      (float *)c->bs + f * n + off);
+            to_real_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((long long)np, c->b0 + f * n + off,
+                                                                      (float *)c->b0r + f * n + off);
+        }
+        c->launches += 16;
         W5_CUDA(c, cudaGetLastError());
-        W5_CUDA(c, cudaMemcpyAsync(c->q0r, c->qs, 5 * n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-        W5_CUDA(c, cudaMemcpyAsync(c->b0r, c->bs, 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     }
     W5_CUDA(c, cudaMemsetAsync(c->flag, 0, 4, c->stream));
     W5_CUDA(c, cudaMemsetAsync(c->hits, 0, 8, c->stream));
@@ -412,18 +562,27 @@ int w5ct_set_state(w5ct_ctx *c, int patch, const double *cons, const double *bfa
 int w5ct_get_state(w5ct_ctx *c, int patch, double *cons, double *bface, double *bcell, int on_device) {
     int rc = check_ready(c);
     if (rc) return rc;
-    if (patch != 0) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
     const size_t n = (size_t)c->n;
+    const PatchGeom g = patch_of(c, patch);
+    const size_t np = (size_t)g.nx * g.ny * g.nz, off = (size_t)g.off;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (cons) W5_CUDA(c, cudaMemcpyAsync(cons, c->q0, 5 * n * 8, kind, c->stream));
-    if (bface) W5_CUDA(c, cudaMemcpyAsync(bface, c->b0, 3 * n * 8, kind, c->stream));
+    if (cons)
+        for (int f = 0; f < 5; ++f)
+            W5_CUDA(c, cudaMemcpyAsync(cons + f * np, c->q0 + f * n + off, np * 8, kind, c->stream));
+    if (bface)
+        for (int f = 0; f < 3; ++f)
+            W5_CUDA(c, cudaMemcpyAsync(bface + f * np, c->b0 + f * n + off, np * 8, kind, c->stream));
     if (bcell) {
         // the FP64 accumulator planes are free between steps
-        cellb_kernel<double><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(
-            c->nx, c->ny, c->nz, c->b0, c->b0 + n, c->b0 + 2 * n, c->acc, c->acc + n, c->acc + 2 * n);
+        const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+        cellb_kernel<double><<<grid, dim3(32, 8), 0, c->stream>>>(g.nx, g.ny, g.nz, c->b0 + off, c->b0 + n + off,
+                                                                  c->b0 + 2 * n + off, c->acc + off, c->acc + n + off,
+                                                                  c->acc + 2 * n + off);
         c->launches++;
         W5_CUDA(c, cudaGetLastError());
-        W5_CUDA(c, cudaMemcpyAsync(bcell, c->acc, 3 * n * 8, kind, c->stream));
+        for (int f = 0; f < 3; ++f)
+            W5_CUDA(c, cudaMemcpyAsync(bcell + f * np, c->acc + f * n + off, np * 8, kind, c->stream));
     }
     int flag = 0;
     rc = read_flag(c, &flag);
@@ -436,7 +595,10 @@ int w5ct_step(w5ct_ctx *c, double dt) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (!(dt > 0.0) || !(dt < 1e300)) return fail(c, W5CT_ERR_ARG, "dt must be finite and > 0 (got %g)", dt);
-    set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt_dev, dt);
+    if (c->npatch > 1)
+        fill_kernel<<<(c->npatch + 127) / 128, 128, 0, c->stream>>>(c->dt_dev, c->npatch, dt);
+    else
+        set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt_dev, dt);
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
     return step_impl(c, c->dt_dev, false);
@@ -456,39 +618,50 @@ int w5ct_step_cfl(w5ct_ctx *c, double *dt_dev_out) {
     if (rc) return rc;
     rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
     if (rc) return rc;
-    dt_kernel<<<1, 1, 0, c->stream>>>(c->smax, c->cfg.cfl, c->dx, c->dy, c->dz, c->dt_dev, dt_dev_out);
-    c->launches++;
-    W5_CUDA(c, cudaGetLastError());
+    rc = launch_dt(c, dt_dev_out);
+    if (rc) return rc;
     return step_impl(c, c->dt_dev, true);
 }
 
 int w5ct_max_signal_speed(w5ct_ctx *c, int patch, double out[3]) {
     int rc = check_ready(c);
     if (rc) return rc;
-    if (patch != 0) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
     if (!out) return fail(c, W5CT_ERR_ARG, "null out");
-    return speeds_impl(c, out);
+    std::vector<double> S(3 * (size_t)c->npatch);
+    rc = speeds_impl(c, S.data());
+    for (int d = 0; d < 3; ++d) out[d] = S[3 * patch + d];
+    return rc;
 }
 
 int w5ct_cfl_dt(w5ct_ctx *c, double *dt) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (!dt) return fail(c, W5CT_ERR_ARG, "null dt");
-    double S[3];
-    rc = speeds_impl(c, S);
+    std::vector<double> S(3 * (size_t)c->npatch);
+    rc = speeds_impl(c, S.data());
     if (rc) return rc;
-    *dt = c->cfg.cfl / (S[0] / c->dx + S[1] / c->dy + S[2] / c->dz);
+    double best = 0.0;
+    for (int p = 0; p < c->npatch; ++p) {
+        const PatchGeom &g = c->pg[p];
+        const double v = c->cfg.cfl / (S[3 * p] / g.dx + S[3 * p + 1] / g.dy + S[3 * p + 2] / g.dz);
+        if (p == 0 || v < best) best = v;
+    }
+    *dt = best;
     return W5CT_OK;
 }
 
 int w5ct_div_b_norm(w5ct_ctx *c, int patch, double *linf, double *l2) {
     int rc = check_ready(c);
     if (rc) return rc;
-    if (patch != 0) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
     if (!linf || !l2) return fail(c, W5CT_ERR_ARG, "null output");
     const size_t n = (size_t)c->n;
-    divb_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->nx, c->ny, c->nz, c->b0, c->b0 + n, c->b0 + 2 * n,
-                                                                   1.0 / c->dx, 1.0 / c->dy, 1.0 / c->dz, c->part);
+    const PatchGeom g = patch_of(c, patch);
+    const size_t off = (size_t)g.off;
+    divb_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(g.nx, g.ny, g.nz, c->b0 + off, c->b0 + n + off,
+                                                                   c->b0 + 2 * n + off, 1.0 / g.dx, 1.0 / g.dy,
+                                                                   1.0 / g.dz, c->part);
     finalize_kernel<<<1, kRedThreads, 0, c->stream>>>(c->part, kRedBlocks, 2, 2, 1u, c->red_out);
     c->launches += 2;
     W5_CUDA(c, cudaGetLastError());
@@ -496,28 +669,75 @@ int w5ct_div_b_norm(w5ct_ctx *c, int patch, double *linf, double *l2) {
     W5_CUDA(c, cudaMemcpyAsync(out, c->red_out, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
     *linf = out[0];
-    *l2 = sqrt(out[1] / (double)c->n);
+    *l2 = sqrt(out[1] / ((double)g.nx * g.ny * g.nz));
     return W5CT_OK;
 }
 
 int w5ct_conserved_totals(w5ct_ctx *c, int patch, double out[8]) {
     int rc = check_ready(c);
     if (rc) return rc;
-    if (patch != 0) return fail(c, W5CT_ERR_ARG, "patch index %d out of range", patch);
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
     if (!out) return fail(c, W5CT_ERR_ARG, "null out");
     const size_t n = (size_t)c->n;
+    const PatchGeom g = patch_of(c, patch);
+    const size_t off = (size_t)g.off;
+    const long long np = (long long)g.nx * g.ny * g.nz;
     const double *pl[8];
-    for (int f = 0; f < 5; ++f) pl[f] = c->q0 + f * n;
-    for (int f = 0; f < 3; ++f) pl[5 + f] = c->b0 + f * n;
+    for (int f = 0; f < 5; ++f) pl[f] = c->q0 + f * n + off;
+    for (int f = 0; f < 3; ++f) pl[5 + f] = c->b0 + f * n + off;
     W5_CUDA(c, cudaMemcpyAsync((void *)c->planes, pl, sizeof(pl), cudaMemcpyHostToDevice, c->stream));
-    sums_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, 8, c->planes, c->part);
+    sums_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(np, 8, c->planes, c->part);
     finalize_kernel<<<1, kRedThreads, 0, c->stream>>>(c->part, kRedBlocks, 8, 8, 0u, c->red_out);
     c->launches += 2;
     W5_CUDA(c, cudaGetLastError());
     W5_CUDA(c, cudaMemcpyAsync(out, c->red_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
-    const double dv = c->dx * c->dy * c->dz;
+    const double dv = g.dx * g.dy * g.dz;
     for (int f = 0; f < 8; ++f) out[f] *= dv;
+    return W5CT_OK;
+}
+
+int w5ct_step_graph(w5ct_ctx *c, int nsteps) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(c, W5CT_ERR_ARG, "nsteps must be >= 0");
+    if (!c->gexec) {
+        // capture one w5ct_step_cfl on a private stream (the legacy default
+        // stream cannot be captured); the graph is then launched on the
+        // context's stream
+        if (!c->cap_stream) W5_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        W5_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaStream_t user = c->stream;
+        const bool timing = c->timing;
+        const long long l0 = c->launches;
+        c->stream = c->cap_stream;
+        c->timing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = w5ct_step_cfl(c, nullptr);
+            e = cudaStreamEndCapture(c->cap_stream, &graph);
+        }
+        c->stream = user;
+        c->timing = timing;
+        c->graph_kernels = c->launches - l0;
+        c->launches = l0;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(c, W5CT_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(c, W5CT_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        W5_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+        c->launches += c->graph_kernels;
+    }
     return W5CT_OK;
 }
 

@@ -60,13 +60,24 @@ struct SweepTile {
     static constexpr int FPT = T2 / 8;    // faces per thread
 };
 
-template <int AX, typename Real, int VAR, int T2, int MINB>
-__global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
+// Patch geometry: cell counts, the patch's first cell in every plane (several
+// patches share the planes back to back) and the inverse spacings.
+struct PatchGeom {
+    int nx, ny, nz, pad;
+    long long off;
+    double rdx, rdy, rdz;     // 1/dx, 1/dy, 1/dz
+    double dx, dy, dz;
+};
+
+// One sweep tile (tile indices tbx, tby, tbz) of the patch described by g.
+// sm: dynamic shared memory of NCQ * NC elements.
+template <int AX, typename Real, int VAR, int T2>
+__device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
+                                           Real *sm) {
     using TT = SweepTile<AX, T2>;
-    extern __shared__ __align__(16) unsigned char w5ct_smem[];
-    Real *sm = reinterpret_cast<Real *>(w5ct_smem);
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int x0 = blockIdx.x * TT::BX, y0 = blockIdx.y * TT::BY, z0 = blockIdx.z * TT::BZ;
+    const int nx = pg.nx, ny = pg.ny, nz = pg.nz;
+    const size_t off = (size_t)pg.off;
+    const int x0 = tbx * TT::BX, y0 = tby * TT::BY, z0 = tbz * TT::BZ;
     const int ox = x0 - (AX == 0 ? 2 : 0), oy = y0 - (AX == 1 ? 2 : 0), oz = z0 - (AX == 2 ? 2 : 0);
     const int tid = threadIdx.x + 32 * threadIdx.y;
 
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
         const int cy = (c / TT::CX) % TT::CY;
         const int cz = c / (TT::CX * TT::CY);
         const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
-        const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+        const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
         cell_fill<Real, AX>(sm + c, TT::NC, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
                             a.bc[0][g], a.bc[1][g], a.bc[2][g], a.K, bad, hit);
     }
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
             const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
             Real Ff[7], s1, s2;
             face_flux<Real, VAR>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
-            const size_t g = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+            const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
             a.F[0][g] = Ff[0];
             a.F[1 + AX][g] = Ff[1];
             a.F[1 + (AX + 1) % 3][g] = Ff[2];
@@ -112,9 +123,45 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
     }
 }
 
+template <int AX, typename Real, int VAR, int T2, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
+    extern __shared__ __align__(16) unsigned char w5ct_smem[];
+    PatchGeom pg;
+    pg.nx = a.nx;
+    pg.ny = a.ny;
+    pg.nz = a.nz;
+    pg.off = 0;
+    sweep_tile<AX, Real, VAR, T2>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<Real *>(w5ct_smem));
+}
+
+// Several patches: block b computes tile tiles[b] = (patch, tbx, tby, tbz).
+template <int AX, typename Real, int VAR, int T2, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_batched_kernel(SweepArgs<Real> a, const PatchGeom *__restrict__ pgs,
+                                                                  const int4 *__restrict__ tiles) {
+    extern __shared__ __align__(16) unsigned char w5ct_smem[];
+    const int4 t = tiles[blockIdx.x];
+    const PatchGeom pg = pgs[t.x];
+    sweep_tile<AX, Real, VAR, T2>(a, pg, t.y, t.z, t.w, reinterpret_cast<Real *>(w5ct_smem));
+}
+
 // ======================================================================
 // cell-centred field: fourth-order interpolation of the faces (Sec. 2.3)
 // ======================================================================
+
+template <typename Real>
+__device__ __forceinline__ void cellb_cell(int nx, int ny, int nz, size_t off, int i, int j, int k,
+                                           const Real *__restrict__ bx, const Real *__restrict__ by,
+                                           const Real *__restrict__ bz, Real *__restrict__ Bx, Real *__restrict__ By,
+                                           Real *__restrict__ Bz) {
+    auto I = [&](int ii, int jj, int kk) -> size_t {
+        return off + (size_t)wrapi(ii, nx) + (size_t)nx * ((size_t)wrapi(jj, ny) + (size_t)ny * (size_t)wrapi(kk, nz));
+    };
+    const size_t p = I(i, j, k);
+    const Real s = Real(1.0 / 16.0);
+    Bx[p] = (Real(9) * (bx[I(i - 1, j, k)] + bx[p]) - (bx[I(i - 2, j, k)] + bx[I(i + 1, j, k)])) * s;
+    By[p] = (Real(9) * (by[I(i, j - 1, k)] + by[p]) - (by[I(i, j - 2, k)] + by[I(i, j + 1, k)])) * s;
+    Bz[p] = (Real(9) * (bz[I(i, j, k - 1)] + bz[p]) - (bz[I(i, j, k - 2)] + bz[I(i, j, k + 1)])) * s;
+}
 
 template <typename Real>
 __global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, const Real *__restrict__ bx,
@@ -122,14 +169,21 @@ __global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, cons
                                                     Real *__restrict__ Bx, Real *__restrict__ By, Real *__restrict__ Bz) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= nx || j >= ny) return;
-    auto I = [&](int ii, int jj, int kk) -> size_t {
-        return (size_t)wrapi(ii, nx) + (size_t)nx * ((size_t)wrapi(jj, ny) + (size_t)ny * (size_t)wrapi(kk, nz));
-    };
-    const size_t p = I(i, j, k);
-    const Real s = Real(1.0 / 16.0);
-    Bx[p] = (Real(9) * (bx[I(i - 1, j, k)] + bx[p]) - (bx[I(i - 2, j, k)] + bx[I(i + 1, j, k)])) * s;
-    By[p] = (Real(9) * (by[I(i, j - 1, k)] + by[p]) - (by[I(i, j - 2, k)] + by[I(i, j + 1, k)])) * s;
-    Bz[p] = (Real(9) * (bz[I(i, j, k - 1)] + bz[p]) - (bz[I(i, j, k - 2)] + bz[I(i, j, k + 1)])) * s;
+    cellb_cell<Real>(nx, ny, nz, 0, i, j, k, bx, by, bz, Bx, By, Bz);
+}
+
+// Several patches: block b covers the 32 x 8 cells of cells[b] = (patch, bx, by, k).
+template <typename Real>
+__global__ void __launch_bounds__(256) cellb_batched_kernel(const PatchGeom *__restrict__ pgs,
+                                                            const int4 *__restrict__ cells, const Real *__restrict__ bx,
+                                                            const Real *__restrict__ by, const Real *__restrict__ bz,
+                                                            Real *__restrict__ Bx, Real *__restrict__ By,
+                                                            Real *__restrict__ Bz) {
+    const int4 t = cells[blockIdx.x];
+    const PatchGeom pg = pgs[t.x];
+    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
+    if (i >= pg.nx || j >= pg.ny) return;
+    cellb_cell<Real>(pg.nx, pg.ny, pg.nz, (size_t)pg.off, i, j, t.w, bx, by, bz, Bx, By, Bz);
 }
 
 // ======================================================================
@@ -166,19 +220,27 @@ struct StageW {
 #define W5CT_UPD_MINB 1
 #endif
 
+// geometry of the patch an update thread works on
+template <typename Real>
+struct UpdGeom {
+    int nx, ny, nz;
+    size_t off;                  // first cell of the patch in every plane
+    Real rdx, rdy, rdz;          // 1/dx etc. (stage arithmetic)
+    double drdx, drdy, drdz;     // 1/dx etc. (final FP64 curl)
+};
+
 template <typename Real, int STAGE>
-__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<Real> a) {
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-    if (i >= nx || j >= ny) return;
+__device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const UpdGeom<Real> &ug, int i, int j, int k,
+                                            double dt) {
+    const int nx = ug.nx, ny = ug.ny, nz = ug.nz;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i + 1 < nx ? i + 1 : 0;
     const int jm = j > 0 ? j - 1 : ny - 1, jp = j + 1 < ny ? j + 1 : 0;
     const int km = k > 0 ? k - 1 : nz - 1, kp = k + 1 < nz ? k + 1 : 0;
+    const size_t off = ug.off;
     auto I = [&](int ii, int jj, int kk) -> size_t {
-        return (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * (size_t)kk);
+        return off + (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * (size_t)kk);
     };
     const size_t p = I(i, j, k);
-    const double dt = *a.dt;
     constexpr double c = StageW<STAGE>::c, wc = StageW<STAGE>::wc;
 
     // Every load of this thread is issued before its first store, so that
@@ -191,8 +253,8 @@ __global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<R
         const size_t pxm = I(im, j, k), pym = I(i, jm, k), pzm = I(i, j, km);
 #pragma unroll
         for (int f = 0; f < 5; ++f)
-            D[f] = (a.Fx[f][pxm] - a.Fx[f][p]) * a.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * a.rdy +
-                   (a.Fz[f][pzm] - a.Fz[f][p]) * a.rdz;
+            D[f] = (a.Fx[f][pxm] - a.Fx[f][p]) * ug.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * ug.rdy +
+                   (a.Fz[f][pzm] - a.Fz[f][p]) * ug.rdz;
     }
 
     // ---- corner EMFs (Eqs. ox1-ox3) from the transport fluxes
@@ -239,9 +301,9 @@ __global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<R
             oav[f] = STAGE == 0 ? 0.0 : a.oacc[f][p];
         }
         // RK stage (Sec. 2.1) and face equations of Sec. 2.3 with this stage's EMFs
-        const Real dbx = -(ox_c - ox_jm) * a.rdy + (oz_c - oz_km) * a.rdz;
-        const Real dby = -(oy_c - oy_km) * a.rdz + (ox_c - ox_im) * a.rdx;
-        const Real dbz = -(oz_c - oz_im) * a.rdx + (oy_c - oy_jm) * a.rdy;
+        const Real dbx = -(ox_c - ox_jm) * ug.rdy + (oz_c - oz_km) * ug.rdz;
+        const Real dby = -(oy_c - oy_km) * ug.rdz + (ox_c - ox_im) * ug.rdx;
+        const Real dbz = -(oz_c - oz_im) * ug.rdx + (oy_c - oy_jm) * ug.rdy;
         const Real cdt = (Real)(c * dt);
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
@@ -271,9 +333,9 @@ __global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<R
         const double az_c = Az[p] + wc * (double)oz_c;
         const double az_km = Az[I(i, j, km)] + wc * (double)oz_km;
         const double az_im = Az[I(im, j, k)] + wc * (double)oz_im;
-        const double dbx = -(ax_c - ax_jm) * a.drdy + (az_c - az_km) * a.drdz;
-        const double dby = -(ay_c - ay_km) * a.drdz + (ax_c - ax_im) * a.drdx;
-        const double dbz = -(az_c - az_im) * a.drdx + (ay_c - ay_jm) * a.drdy;
+        const double dbx = -(ax_c - ax_jm) * ug.drdy + (az_c - az_km) * ug.drdz;
+        const double dby = -(ay_c - ay_km) * ug.drdz + (ax_c - ax_im) * ug.drdx;
+        const double dbz = -(az_c - az_im) * ug.drdx + (ay_c - ay_jm) * ug.drdy;
         // last stage: q^{n+1} = q0 + dt sum_k w_k c_k D_k and the final CT update
         constexpr bool kCopy = !std::is_same<Real, double>::value;   // float copy of q^{n+1}, b^{n+1}
 #pragma unroll
@@ -291,6 +353,30 @@ __global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<R
             if (kCopy) a.b0r[f][p] = (Real)bn[f];
         }
     }
+}
+
+template <typename Real, int STAGE>
+__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<Real> a) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= a.nx || j >= a.ny) return;
+    const UpdGeom<Real> ug = {a.nx, a.ny, a.nz, 0, a.rdx, a.rdy, a.rdz, a.drdx, a.drdy, a.drdz};
+    update_cell<Real, STAGE>(a, ug, i, j, k, *a.dt);
+}
+
+// Several patches: block b updates the 32 x 8 cells of cells[b] = (patch, bx,
+// by, k) with that patch's dt, dts[patch].
+template <typename Real, int STAGE>
+__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_batched_kernel(UpdateArgs<Real> a,
+                                                                            const PatchGeom *__restrict__ pgs,
+                                                                            const int4 *__restrict__ cells,
+                                                                            const double *__restrict__ dts) {
+    const int4 t = cells[blockIdx.x];
+    const PatchGeom pg = pgs[t.x];
+    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
+    if (i >= pg.nx || j >= pg.ny) return;
+    const UpdGeom<Real> ug = {pg.nx, pg.ny, pg.nz, (size_t)pg.off, (Real)pg.rdx, (Real)pg.rdy, (Real)pg.rdz,
+                              pg.rdx, pg.rdy, pg.rdz};
+    update_cell<Real, STAGE>(a, ug, i, j, t.w, dts[t.x]);
 }
 
 // ======================================================================
@@ -331,6 +417,21 @@ __device__ __forceinline__ void block_reduce(T (&v)[N], bool is_max[N], T *red /
     }
 }
 
+// |v_d| + c_f^d of one cell for d = x, y, z folded into v (Eq. cfl)
+template <typename Real>
+__device__ __forceinline__ void cell_speeds(Real r, Real m0, Real m1, Real m2, Real E, Real bx, Real by, Real bz,
+                                            const Phys<Real> &K, double (&v)[3], bool &bad) {
+    if (K.floors && r < K.rho_min) r = K.rho_min;
+    const Real ir = M<Real>::rcp_(r);
+    const Real vx = m0 * ir, vy = m1 * ir, vz = m2 * ir;
+    Real P = K.gm1 * (E - Real(0.5) * r * (vx * vx + vy * vy + vz * vz) - Real(0.5) * (bx * bx + by * by + bz * bz));
+    if (K.floors && P < K.p_min) P = K.p_min;
+    if (!(r > Real(0)) || !M<Real>::finite_pos(P)) bad = true;
+    v[0] = fmax(v[0], (double)signal_speed<Real>(r, vx, P, bx, by, bz, K));
+    v[1] = fmax(v[1], (double)signal_speed<Real>(r, vy, P, by, bz, bx, K));
+    v[2] = fmax(v[2], (double)signal_speed<Real>(r, vz, P, bz, bx, by, K));
+}
+
 // |v_d| + c_f^d maxima of the stage state (Eq. cfl)
 template <typename Real>
 __global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx, int ny, const Real *q0, const Real *q1,
@@ -340,19 +441,8 @@ __global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx,
     __shared__ double red[3 * 32];
     double v[3] = {0.0, 0.0, 0.0};
     bool bad = false;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-        Real r = q0[p];
-        if (K.floors && r < K.rho_min) r = K.rho_min;
-        const Real ir = M<Real>::rcp_(r);
-        const Real vx = q1[p] * ir, vy = q2[p] * ir, vz = q3[p] * ir;
-        const Real bx = B0[p], by = B1[p], bz = B2[p];
-        Real P = K.gm1 * (q4[p] - Real(0.5) * r * (vx * vx + vy * vy + vz * vz) - Real(0.5) * (bx * bx + by * by + bz * bz));
-        if (K.floors && P < K.p_min) P = K.p_min;
-        if (!(r > Real(0)) || !M<Real>::finite_pos(P)) bad = true;
-        v[0] = fmax(v[0], (double)signal_speed<Real>(r, vx, P, bx, by, bz, K));
-        v[1] = fmax(v[1], (double)signal_speed<Real>(r, vy, P, by, bz, bx, K));
-        v[2] = fmax(v[2], (double)signal_speed<Real>(r, vz, P, bz, bx, by, K));
-    }
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        cell_speeds<Real>(q0[p], q1[p], q2[p], q3[p], q4[p], B0[p], B1[p], B2[p], K, v, bad);
     if (bad) atomicOr(flag, 1);
     bool ismax[3] = {true, true, true};
     block_reduce<double, 3>(v, ismax, red);
@@ -362,6 +452,66 @@ __global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx,
         atomicMax(&smax[1], (unsigned long long)__double_as_longlong(v[1]));
         atomicMax(&smax[2], (unsigned long long)__double_as_longlong(v[2]));
     }
+}
+
+// Several patches: block b covers the 32 x 8 cells of cells[b] = (patch, bx,
+// by, k); the maxima of patch p go to smax[3 p .. 3 p + 2] (zeroed before).
+template <typename Real>
+__global__ void __launch_bounds__(256) speed_batched_kernel(const PatchGeom *__restrict__ pgs,
+                                                            const int4 *__restrict__ cells, const Real *q0,
+                                                            const Real *q1, const Real *q2, const Real *q3,
+                                                            const Real *q4, const Real *B0, const Real *B1,
+                                                            const Real *B2, Phys<Real> K, unsigned long long *smax,
+                                                            int *flag) {
+    const int4 t = cells[blockIdx.x];
+    const PatchGeom pg = pgs[t.x];
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
+    double v[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    if (i < pg.nx && j < pg.ny) {
+        const size_t p = (size_t)pg.off + (size_t)i + (size_t)pg.nx * ((size_t)j + (size_t)pg.ny * (size_t)t.w);
+        cell_speeds<Real>(q0[p], q1[p], q2[p], q3[p], q4[p], B0[p], B1[p], B2[p], K, v, bad);
+    }
+    if (bad) atomicOr(flag, 1);
+    // block maxima over the 8 warps of the 32 x 8 block
+    __shared__ double red2[3 * 32];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+    if ((tid & 31) == 0)
+        for (int q = 0; q < 3; ++q) red2[q * 32 + (tid >> 5)] = v[q];
+    __syncthreads();
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double x = tid < 8 ? red2[q * 32 + tid] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+            if (tid == 0) atomicMax(&smax[3 * t.x + q], (unsigned long long)__double_as_longlong(x));
+        }
+    }
+}
+
+// dt of every patch, as dt_kernel: dts[p] = CFL / sum_d (S_d / dx_d)
+static __global__ void dt_batched_kernel(const PatchGeom *__restrict__ pgs, int npatch,
+                                         const unsigned long long *smax, double cfl, double *dts, double *dts_copy) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npatch) return;
+    const double s0 = __longlong_as_double((long long)smax[3 * p + 0]);
+    const double s1 = __longlong_as_double((long long)smax[3 * p + 1]);
+    const double s2 = __longlong_as_double((long long)smax[3 * p + 2]);
+    const PatchGeom pg = pgs[p];
+    const double sum = __dadd_rn(__dadd_rn(__ddiv_rn(s0, pg.dx), __ddiv_rn(s1, pg.dy)), __ddiv_rn(s2, pg.dz));
+    const double v = __ddiv_rn(cfl, sum);
+    dts[p] = v;
+    if (dts_copy) dts_copy[p] = v;
+}
+
+static __global__ void fill_kernel(double *dst, int n, double v) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) dst[p] = v;
 }
 
 // dt = CFL / sum_d (S_d / dx_d), with the same rounded operations as the

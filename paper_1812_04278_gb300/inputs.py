@@ -366,3 +366,35 @@ def blast_turbulence_state(N, seed=1815, seed_b=1816, mach=5.0, p_amb=0.1, p_bla
     # raise the pressure inside the sphere: E grows by (p_blast - p_amb)/(gamma - 1)
     cons[4] += np.where(inside, (p_blast - p_amb) / (gamma - 1.0), 0.0)
     return cons, bface
+
+
+PATCH_SIZES = (16, 24, 32, 48, 64)
+
+
+def patch_batch_spec(npatch=512, seed=1803, sizes=PATCH_SIZES, mach=(0.5, 3.0), beta=(0.1, 10.0)):
+    """Sizes and turbulence parameters of a batch of independent periodic
+    patches: each of (nx, ny, nz) drawn uniformly from `sizes`, rms Mach
+    uniform in `mach`, beta log-uniform in `beta`, mean field along a random
+    unit vector, and two seeds per patch for its velocity and field draws.
+    Every patch is a unit box (dx = 1/nx, dy = 1/ny, dz = 1/nz)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(npatch):
+        shape = tuple(int(s) for s in rng.choice(np.asarray(sizes), size=3))
+        m = float(rng.uniform(mach[0], mach[1]))
+        b = float(np.exp(rng.uniform(np.log(beta[0]), np.log(beta[1]))))
+        d = rng.standard_normal(3)
+        d = d / np.linalg.norm(d)
+        s1, s2 = (int(v) for v in rng.integers(1 << 30, size=2))
+        out.append(dict(shape=shape, dx=tuple(1.0 / n for n in shape), mach=m, beta=b, B_dir=tuple(float(v) for v in d),
+                        seed=s1, seed_b=s2))
+    return out
+
+
+def patch_state(spec, gamma=GAMMA, dB_frac=0.1, kmin=2):
+    """Turbulent state of one patch of patch_batch_spec: rho = 1, P = 1/gamma,
+    k^-5/3 velocity and field perturbation for kmin <= |k| <= min(n)/2 - 1."""
+    kmax = min(spec["shape"]) // 2 - 1
+    return turbulent_state(None, seed=spec["seed"], seed_b=spec["seed_b"], mach=spec["mach"], beta=spec["beta"],
+                           dB_frac=dB_frac, kmin=kmin, kmax=kmax, gamma=gamma, B_dir=spec["B_dir"],
+                           shape=spec["shape"])

@@ -40,7 +40,7 @@ EXPORTED = [
     "w5ct_set_state", "w5ct_get_state", "w5ct_step", "w5ct_step_dev", "w5ct_step_cfl",
     "w5ct_max_signal_speed", "w5ct_cfl_dt", "w5ct_div_b_norm", "w5ct_conserved_totals",
     "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
-    "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc",
+    "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc", "w5ct_step_graph",
 ]
 W5CT_NOALLOC_MAX_CELLS = 134217728
 
@@ -64,6 +64,7 @@ _sig = {
     "w5ct_step": [_VP, c_double],
     "w5ct_step_dev": [_VP, _VP],
     "w5ct_step_cfl": [_VP, _VP],
+    "w5ct_step_graph": [_VP, c_int],
     "w5ct_max_signal_speed": [_VP, c_int, _DP],
     "w5ct_cfl_dt": [_VP, _DP],
     "w5ct_div_b_norm": [_VP, c_int, _DP, _DP],
@@ -135,9 +136,17 @@ def w5ct_set_stream(ctx, stream: int):
     _check(_lib.w5ct_set_stream(ctx, stream), "w5ct_set_stream", ctx)
 
 
-def w5ct_init_grid(ctx, n3, dx3, npatch: int = 1):
-    n = (c_int * 3)(*[int(v) for v in n3])
-    d = (c_double * 3)(*[float(v) for v in dx3])
+def w5ct_init_grid(ctx, n3, dx3, npatch: int | None = None):
+    """n3, dx3: one (nx, ny, nz) / (dx, dy, dz) triple, or npatch of them
+    (nested or flattened); npatch defaults to the number of triples."""
+    nf = [int(v) for v in np.asarray(n3).reshape(-1)]
+    df = [float(v) for v in np.asarray(dx3, dtype=np.float64).reshape(-1)]
+    if npatch is None:
+        npatch = len(nf) // 3
+    if len(nf) != 3 * max(npatch, 1) or len(df) != 3 * max(npatch, 1):
+        raise ValueError(f"w5ct_init_grid: {npatch} patches need 3 sizes and 3 spacings each")
+    n = (c_int * len(nf))(*nf)
+    d = (c_double * len(df))(*df)
     _check(_lib.w5ct_init_grid(ctx, npatch, n, d), "w5ct_init_grid", ctx)
 
 
@@ -160,6 +169,10 @@ def w5ct_step_dev(ctx, dt_dev):
 
 def w5ct_step_cfl(ctx, dt_dev_out=None):
     _check(_lib.w5ct_step_cfl(ctx, _addr(dt_dev_out)), "w5ct_step_cfl", ctx)
+
+
+def w5ct_step_graph(ctx, nsteps: int):
+    _check(_lib.w5ct_step_graph(ctx, int(nsteps)), "w5ct_step_graph", ctx)
 
 
 def w5ct_max_signal_speed(ctx, patch: int = 0) -> np.ndarray:
@@ -302,6 +315,77 @@ class Solver:
 
     def conserved_totals(self):
         return w5ct_conserved_totals(self.ctx)
+
+    def status(self):
+        return w5ct_status(self.ctx)
+
+    def synchronize(self):
+        w5ct_synchronize(self.ctx)
+
+
+class Batch:
+    """Several independent periodic patches advanced together by one context
+    (every launch covers the tiles of all patches; w5ct_step_graph replays a
+    captured step)."""
+
+    def __init__(self, shapes, dxs, cfg: w5ct_config | None = None, stream: int | None = None):
+        cfg = cfg if cfg is not None else make_config()
+        if stream is not None:
+            cfg.stream = stream
+        self.cfg = cfg
+        self.ctx = w5ct_create(cfg)
+        self.shapes = [tuple(int(s) for s in sh) for sh in shapes]
+        self.dxs = [tuple(float(d) for d in dx) for dx in dxs]
+        self.npatch = len(self.shapes)
+        w5ct_init_grid(self.ctx, self.shapes, self.dxs, npatch=self.npatch)
+
+    def close(self):
+        if self.ctx:
+            w5ct_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, p, cons, bface):
+        if isinstance(cons, np.ndarray):
+            w5ct_set_state(self.ctx, np.ascontiguousarray(cons, dtype=np.float64),
+                           np.ascontiguousarray(bface, dtype=np.float64), 0, patch=p)
+        else:
+            w5ct_set_state(self.ctx, cons.contiguous(), bface.contiguous(), 1, patch=p)
+
+    def get_state(self, p):
+        nx, ny, nz = self.shapes[p]
+        cons = np.empty((5, nz, ny, nx))
+        bface = np.empty((3, nz, ny, nx))
+        bcell = np.empty((3, nz, ny, nx))
+        w5ct_get_state(self.ctx, cons, bface, bcell, 0, patch=p)
+        return cons, bface, bcell
+
+    def step(self, dt):
+        w5ct_step(self.ctx, dt)
+
+    def step_dev(self, dts_dev):
+        """One step, patch p taking dts_dev[p] (device buffer of npatch doubles)."""
+        w5ct_step_dev(self.ctx, dts_dev)
+
+    def step_cfl(self, dt_dev_out=None):
+        w5ct_step_cfl(self.ctx, dt_dev_out)
+
+    def step_graph(self, nsteps):
+        w5ct_step_graph(self.ctx, nsteps)
+
+    def max_signal_speed(self, p):
+        return w5ct_max_signal_speed(self.ctx, p)
+
+    def div_b_norm(self, p):
+        return w5ct_div_b_norm(self.ctx, p)
+
+    def conserved_totals(self, p):
+        return w5ct_conserved_totals(self.ctx, p)
 
     def status(self):
         return w5ct_status(self.ctx)

@@ -61,9 +61,14 @@ def test_create_and_destroy_without_device_work(w5):
         w5.w5ct_step(ctx, 0.1)            # no grid yet: rejected on the host
     assert e.value.code == w5.W5CT_ERR_ARG or e.value.code == w5.W5CT_ERR_STATE
     with pytest.raises(w5.W5ctError) as e:
-        w5.w5ct_init_grid(ctx, (8, 8, 8), (0.1, 0.1, 0.1), npatch=2)
-    assert e.value.code == w5.W5CT_ERR_UNSUPPORTED
+        w5.w5ct_init_grid(ctx, (8, 8, 8), (0.1, 0.1, 0.1), npatch=0)
+    assert e.value.code == w5.W5CT_ERR_ARG
     with pytest.raises(w5.W5ctError) as e:
         w5.w5ct_init_grid(ctx, (0, 8, 8), (0.1, 0.1, 0.1))
     assert e.value.code == w5.W5CT_ERR_ARG
+    with pytest.raises(w5.W5ctError) as e:      # second patch invalid
+        w5.w5ct_init_grid(ctx, [(8, 8, 8), (4, -1, 4)], [(0.1, 0.1, 0.1)] * 2)
+    assert e.value.code == w5.W5CT_ERR_ARG
+    with pytest.raises(ValueError):             # buffers shorter than 3 x npatch
+        w5.w5ct_init_grid(ctx, (8, 8, 8), (0.1, 0.1, 0.1), npatch=2)
     w5.w5ct_destroy(ctx)

@@ -1,0 +1,169 @@
+"""Several patches advanced by one context (batched launches over a tile
+table, per-patch dt, graph replay), through the C ABI.
+
+Every patch of a batch runs the same per-cell and per-face arithmetic as a
+context holding that patch alone, so the batched results must equal the
+single-patch ones bit for bit; FP64 batches are also checked against the
+oracle to 1e-12 per step (the bound of the single-patch parity tests).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+# uneven sizes: ragged x tiles, patches smaller than one tile, ny below the
+# stencil width, and one patch spanning several tiles in every direction
+SHAPES = [(16, 16, 16), (24, 16, 32), (33, 9, 10), (8, 8, 8), (48, 24, 16), (12, 3, 17)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1812_04278_gb300 import build
+    build.build()
+    from paper_1812_04278_gb300 import inputs, w5ct
+    oracle.build()
+    return dict(torch=torch, O=oracle, I=inputs, W=w5ct)
+
+
+def states(env, shapes, seed0):
+    I = env["I"]
+    return [I.random_smooth_state(sh, seed=seed0 + p) for p, sh in enumerate(shapes)]
+
+
+def spacings(shapes):
+    return [tuple(1.0 / n for n in sh) for sh in shapes]
+
+
+def make_batch(env, shapes, sts, precision, variant):
+    W, torch = env["W"], env["torch"]
+    b = W.Batch(shapes, spacings(shapes), W.make_config(precision=precision, weno_variant=variant),
+                stream=torch.cuda.current_stream().cuda_stream)
+    for p, (cons, bface) in enumerate(sts):
+        b.set_state(p, cons, bface)
+    return b
+
+
+def make_single(env, shape, st, precision, variant):
+    W, torch = env["W"], env["torch"]
+    s = W.Solver(shape, tuple(1.0 / n for n in shape), W.make_config(precision=precision, weno_variant=variant),
+                 stream=torch.cuda.current_stream().cuda_stream)
+    s.set_state(*st)
+    return s
+
+
+def assert_same(a, b, what):
+    for x, y, name in zip(a, b, ("cons", "bface", "bcell")):
+        assert np.array_equal(x, y), (what, name, np.abs(x - y).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batched_step_equals_single_patches(env, precision, variant):
+    sts = states(env, SHAPES, 100 + 10 * precision + variant)
+    b = make_batch(env, SHAPES, sts, precision, variant)
+    dt = 0.2 * min(1.0 / n for sh in SHAPES for n in sh)
+    for _ in range(2):
+        b.step(dt)
+    for p, sh in enumerate(SHAPES):
+        s = make_single(env, sh, sts[p], precision, variant)
+        for _ in range(2):
+            s.step(dt)
+        assert_same(b.get_state(p), s.get_state(), ("patch", p, sh))
+        s.close()
+    b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp64_batch_matches_oracle(env, variant):
+    O = env["O"]
+    sts = states(env, SHAPES, 200 + variant)
+    b = make_batch(env, SHAPES, sts, 0, variant)
+    oras = []
+    for p, sh in enumerate(SHAPES):
+        o = O.Oracle(sh, tuple(1.0 / n for n in sh), O.make_config(weno_variant=variant))
+        o.set_state(*sts[p])
+        oras.append(o)
+    dts = [o.cfl_dt() for o in oras]
+    torch = env["torch"]
+    dts_dev = torch.tensor(dts, dtype=torch.float64, device="cuda")
+    b.step_dev(dts_dev)
+    for p, o in enumerate(oras):
+        o.step(dts[p])
+        gc, gb, _ = b.get_state(p)
+        oc, ob, _ = o.get_state()
+        S = max(np.abs(oc).max(), np.abs(ob).max())
+        err = max(np.abs(gc - oc).max(), np.abs(gb - ob).max()) / S
+        assert err <= TOL64, (p, SHAPES[p], err)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_per_patch_cfl_dt(env, precision):
+    """step_cfl gives every patch the dt its own state fixes (Eq. cfl), equal
+    to the dt a context of that patch alone computes."""
+    torch = env["torch"]
+    sts = states(env, SHAPES, 300 + precision)
+    b = make_batch(env, SHAPES, sts, precision, 1)
+    dts = torch.zeros(len(SHAPES), dtype=torch.float64, device="cuda")
+    b.step_cfl(dts)
+    dts_b = dts.cpu().numpy()
+    assert len(set(dts_b.tolist())) == len(SHAPES)     # the patches take different dts
+    for p, sh in enumerate(SHAPES):
+        s = make_single(env, sh, sts[p], precision, 1)
+        d1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.step_cfl(d1)
+        assert d1.item() == dts_b[p], (p, d1.item(), dts_b[p])
+        assert_same(b.get_state(p), s.get_state(), ("patch", p, sh))
+        s.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_eager_steps(env, precision):
+    sts = states(env, SHAPES, 400 + precision)
+    a = make_batch(env, SHAPES, sts, precision, 1)
+    e = make_batch(env, SHAPES, sts, precision, 1)
+    a.step_graph(2)
+    a.step_graph(1)           # reuses the captured graph
+    for _ in range(3):
+        e.step_cfl()
+    a.synchronize()
+    e.synchronize()
+    for p in range(len(SHAPES)):
+        assert_same(a.get_state(p), e.get_state(p), ("patch", p))
+    assert a.status()[1] == 0 and e.status()[1] == 0       # no non-physical state flagged
+    a.close()
+    e.close()
+
+
+def test_batched_diagnostics_are_per_patch(env):
+    sts = states(env, SHAPES, 500)
+    b = make_batch(env, SHAPES, sts, 0, 1)
+    b.step_cfl()
+    b.synchronize()
+    for p, sh in enumerate(SHAPES):
+        s = make_single(env, sh, sts[p], 0, 1)
+        s.step_cfl()
+        assert np.array_equal(b.max_signal_speed(p), s.max_signal_speed())
+        linf_b, l2_b = b.div_b_norm(p)
+        linf_s, l2_s = s.div_b_norm()
+        assert linf_b == linf_s and abs(l2_b - l2_s) <= 1e-14 * max(l2_s, 1e-300)
+        np.testing.assert_allclose(b.conserved_totals(p), s.conserved_totals(), rtol=1e-13, atol=1e-15)
+        s.close()
+    b.close()
+
+
+def test_batch_rejects_bad_patch_index(env):
+    W = env["W"]
+    sts = states(env, SHAPES[:2], 600)
+    b = make_batch(env, SHAPES[:2], sts, 0, 1)
+    with pytest.raises(W.W5ctError) as e:
+        W.w5ct_max_signal_speed(b.ctx, 2)
+    assert e.value.code == W.W5CT_ERR_ARG
+    b.close()
