@@ -674,7 +674,7 @@ def run_batched(args):
         "data": "synthetic",
         "config": {"workload": f"{npatch} independent periodic unit-box patches, each of nx, ny, nz uniform in "
                                f"{{16,24,32,48,64}} (seed 1803); per patch: rho=1, P=1/gamma, k^-5/3 turbulence "
-                               f"(2 <= k <= min(n)/2-1) at rms Mach U[0.5,3], beta log-uniform [0.1,10], mean B "
+                               f"(2 <= k <= max(2, min(n)/8)) at rms Mach U[0.5,3], beta log-uniform [0.1,10], mean B "
                                f"along a random unit vector; own dt per patch; WENO-Z, CFL 0.8, floors rho, P >= 1e-8; "
                                f"one CUDA graph replay per step", "zones": zones, "patches": npatch,
                    "patch_cells_min": int(sizes.min()), "patch_cells_max": int(sizes.max()),

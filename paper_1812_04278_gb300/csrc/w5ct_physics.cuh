@@ -41,6 +41,9 @@ struct Phys {
     Real eps_b;                  // eps_B of Appendix A
     Real eps_b2;                 // threshold on c_f^2 - c_slow^2 (eps_B^2, >= FLT_MIN in float)
     Real rho_min, p_min;
+    // lower bound on c_s^2 in the interface eigenvectors, relative to
+    // v^2 + c_A^2 + b_t^2 (0 in double; see face_flux)
+    Real cs2_rel;
     int floors;
 };
 
@@ -365,10 +368,19 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
 
     // ---- eigen scalars at the interface state (Appendix A)
     const Real ir = m::rcp_(r);
-    const Real cs2 = K.gamma * P * ir;
     const Real ca2 = Bn * Bn * ir;
     const Real btm = Bt1 * Bt1 + Bt2 * Bt2;
     const Real bt2 = btm * ir;
+    const Real v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    // The slow and fast left eigenvectors carry 1/(2 c_s^2): the projection
+    // amplifies the rounding of the data by about (v^2 + c_A^2 + b_t^2)/c_s^2.
+    // In float, near a pressure floor, that reaches 1e9 and the split fluxes
+    // drown in rounding, so the eigenvectors (never the LF speeds) take c_s^2
+    // no smaller than cs2_rel times that sum.  L and R stay exact inverses, so
+    // the flux stays consistent and conservative; only the basis in which
+    // WENO reconstructs changes.  cs2_rel = 0 in double.
+    Real cs2 = K.gamma * P * ir;
+    if constexpr (std::is_same<Real, float>::value) cs2 = m::max_(cs2, K.cs2_rel * (v2 + ca2 + bt2));
     Real fmc, cms, cf2, csl2;
     speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
     const Real cf = m::sqrt_(cf2), csl = m::sqrt_(csl2), cs = m::sqrt_(cs2);
@@ -394,7 +406,6 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     const Real sg = (Bn >= K.eps_b) ? Real(1) : Real(-1);
     const Real sr = m::sqrt_(r);
     const Real isr = sr * ir;
-    const Real v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
     const Real bv = b1 * vt1 + b2 * vt2;
     const Real Gf = af * cf * vn - as * csl * sg * bv;
     const Real Ga = sg * (b2 * vt1 - b1 * vt2);

@@ -393,8 +393,9 @@ def patch_batch_spec(npatch=512, seed=1803, sizes=PATCH_SIZES, mach=(0.5, 3.0), 
 
 def patch_state(spec, gamma=GAMMA, dB_frac=0.1, kmin=2):
     """Turbulent state of one patch of patch_batch_spec: rho = 1, P = 1/gamma,
-    k^-5/3 velocity and field perturbation for kmin <= |k| <= min(n)/2 - 1."""
-    kmax = min(spec["shape"]) // 2 - 1
+    k^-5/3 velocity and field perturbation for kmin <= |k| <= max(kmin, min(n)/8)
+    (wavelengths of at least 8 cells, as 2 <= k <= 32 on a 256^3 grid)."""
+    kmax = max(kmin, min(spec["shape"]) // 8)
     return turbulent_state(None, seed=spec["seed"], seed_b=spec["seed_b"], mach=spec["mach"], beta=spec["beta"],
                            dB_frac=dB_frac, kmin=kmin, kmax=kmax, gamma=gamma, B_dir=spec["B_dir"],
                            shape=spec["shape"])
