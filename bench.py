@@ -584,35 +584,56 @@ def run_batched(args):
     npatch = len(specs)
     stream = torch.cuda.current_stream()
 
-    def make(precision):
-        b = w5.Batch(shapes, dxs, w5.make_config(precision=precision, floors=1), stream=stream.cuda_stream)
+    def reset(b):
         for p, (c, f) in enumerate(states):
             b.set_state(p, c, f)
+
+    def make(precision):
+        b = w5.Batch(shapes, dxs, w5.make_config(precision=precision, floors=1), stream=stream.cuda_stream)
+        reset(b)
         return b
 
-    # ---- FP32-bulk, graph replay (headline)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def graph_steps(b, nsteps):
+        e0.record(stream)
+        b.step_graph(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # ---- FP32-bulk, graph replay (headline): tile shapes from the model,
+    # then from the measuring autotuner; each timed run starts from the
+    # initial state (the supersonic patches stay physical for about 15 steps
+    # from it; the scheme has no protection fluxes)
     b32 = make(w5.W5CT_FP32_BULK)
+    b32.step_graph(args.warmup)
+    torch.cuda.synchronize()
+    ms_model = graph_steps(b32, args.steps)
+    bad_model = b32.status()[1]
+    tiles_model = b32.tile_variants().tolist()
+    t0 = time.perf_counter()
+    b32.autotune(w5.W5CT_TUNE_MEASURE, 3)
+    tune_s = time.perf_counter() - t0
+    tiles_tuned = b32.tile_variants().tolist()
+    reset(b32)
     b32.step_graph(args.warmup)
     torch.cuda.synchronize()
     launches0 = w5.w5ct_launch_count(b32.ctx)
     sampler = ClockSampler(0)
     sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b32.step_graph(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms32 = graph_steps(b32, args.steps)
     clocks = sampler.stop()
-    ms32 = e0.elapsed_time(e1)
     launches = w5.w5ct_launch_count(b32.ctx) - launches0
+    hits, bad = b32.status()
     # per-launch time of the sweeps (eager steps with the launch timers on)
+    reset(b32)
     w5.w5ct_set_timing(b32.ctx, True)
     for _ in range(2):
         b32.step_cfl()
     torch.cuda.synchronize()
     nsw, swms = w5.w5ct_sweep_timing(b32.ctx)
     w5.w5ct_set_timing(b32.ctx, False)
-    hits, bad = b32.status()
     divb32 = max(b32.div_b_norm(p)[0] for p in range(npatch))
     b32.close()
 
@@ -620,6 +641,8 @@ def run_batched(args):
     ne = args.err_steps
     dts = torch.zeros((ne, npatch), dtype=torch.float64, device="cuda")
     b64 = make(w5.W5CT_FP64)
+    torch.cuda.synchronize()
+    b64.autotune(w5.W5CT_TUNE_MEASURE, 1)
     torch.cuda.synchronize()
     e0.record(stream)
     for k in range(ne):
@@ -687,9 +710,13 @@ def run_batched(args):
                          "div_b_linf": divb64},
         "l1_fp32_vs_fp64": {"mean": float(np.mean(l1s)), "max": float(np.max(l1s)), "steps": ne,
                             "fp64_change_mean": float(np.mean(l1c))},
+        "tiles": {"variants": "0: 32x16, 1: 16x16, 2: 8x16, 3: 8x8 (lanes along x x faces)",
+                  "patches_per_axis_and_variant_tuned": tiles_tuned,
+                  "patches_per_axis_and_variant_model": tiles_model,
+                  "model_value": zones * args.steps / (ms_model * 1e-3), "autotune_seconds": tune_s},
         "unbatched_fp32": {"value": zones * nu / (msu * 1e-3), "ms_per_step": msu / nu, "steps": nu,
                            "contexts": npatch},
-        "floor_hits": hits, "nonphysical": bad, "div_b_linf": divb32,
+        "floor_hits": hits, "nonphysical": bad + bad_model, "div_b_linf": divb32,
         "gpu_launches": launches, "clocks": clocks, "kernel_src": kernel_source_hash(),
     }
     print(json.dumps(line))

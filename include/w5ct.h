@@ -98,7 +98,8 @@ int w5ct_set_stream(w5ct_ctx *ctx, void *stream);
  * n3 = {nx, ny, nz} per patch (npatch x 3 ints, each >= 1) and dx3 = {dx, dy,
  * dz} per patch (npatch x 3 doubles > 0), host pointers.  With npatch > 1
  * every step advances all patches together, each kernel launch covering the
- * tiles of every patch.  Previous buffers are freed. */
+ * tiles of every patch; each patch then holds at most 2^30 cells.  Previous
+ * buffers are freed. */
 int w5ct_init_grid(w5ct_ctx *ctx, int npatch, const int *n3, const double *dx3);
 
 /* Load the state q^n of patch `patch` (0 .. npatch-1): cons (5 planes) and
@@ -135,6 +136,30 @@ int w5ct_step_cfl(w5ct_ctx *ctx, double *dt_dev_out);
  * calls reuse; the graph is launched on the context's stream.  The graph is
  * dropped by w5ct_init_grid and w5ct_destroy.  Asynchronous. */
 int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
+
+/* Tile shapes of the batched sweeps (npatch > 1; no counterpart in the
+ * paper, whose sweeps run over one patch's pencils).  Each patch is swept
+ * along each axis in tiles of BX cells along x times T2 faces or pencils in
+ * the second direction, one of these variants:
+ *   0: BX = 32, T2 = 16 (FP32_BULK) or 8 (FP64, x-sweep) / 16 (FP64, y, z)
+ *   1: BX = 16, T2 = 16      2: BX = 8, T2 = 16      3: BX = 8, T2 = 8
+ * (variants 1-3 in FP32_BULK only).  The variant changes only which threads
+ * compute a face, never its arithmetic: results are bit for bit the same.
+ * mode = W5CT_TUNE_MEASURE times every variant on every class of patches
+ * with the same (nx, ny) (x- and y-sweeps) or (nx, nz) (z-sweep) on the
+ * current state, `reps` timed launches each, and keeps the fastest per class
+ * (synchronises; needs a state; the flux buffers are overwritten, counters
+ * kept).  mode = W5CT_TUNE_MODEL (the choice w5ct_init_grid makes) takes
+ * the variant with the fewest padded lanes and rows per face.  mode = v >= 0
+ * forces variant v on every patch.  A captured step graph is dropped.  With
+ * npatch = 1 this does nothing and returns W5CT_OK. */
+#define W5CT_TUNE_MEASURE (-1)
+#define W5CT_TUNE_MODEL (-2)
+int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
+
+/* out[3] = {variant, BX, T2} of the tiles that sweep patch `patch` along
+ * `axis` (0, 1, 2).  Host only. */
+int w5ct_tile_variant(w5ct_ctx *ctx, int axis, int patch, int out[3]);
 
 /* For patch `patch`: S_d = max over its cells of |v_d| + c_fast^d for d = x, y, z (Eq. cfl; the
  * fast speed of Eq. fast with B_n = B_d), out[3] on the host.  Synchronises.

@@ -3,7 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "w5ct.h"
@@ -49,9 +51,14 @@ struct w5ct_ctx {
     int npatch = 0;
     std::vector<PatchGeom> pg;       // host copy of the patch table
     PatchGeom *pg_dev = nullptr;     // device patch table
-    int4 *tiles_dev[3] = {nullptr, nullptr, nullptr};   // sweep tiles per axis
-    int ntiles[3] = {0, 0, 0};
-    int4 *cells_dev = nullptr;       // 32 x 8 cell blocks of every patch
+    // sweep tiles: per axis, the patches' tiles grouped by tile variant
+    // (segment [seg_off, seg_off + seg_n) of tiles_buf); pvar[axis][p] is
+    // the variant of patch p
+    std::vector<signed char> pvar[3];
+    int4 *tiles_buf = nullptr;
+    int seg_off[3][kMaxTileVariants] = {};
+    int seg_n[3][kMaxTileVariants] = {};
+    int4 *cells_dev = nullptr;       // 256-cell blocks of every patch
     int ncells = 0;
     // captured step (w5ct_step_graph)
     cudaStream_t cap_stream = nullptr;
@@ -121,6 +128,9 @@ void free_grid(w5ct_ctx *c) {
     c->graph_kernels = 0;
     if (c->slab) cudaFree(c->slab);
     c->slab = nullptr;
+    if (c->tiles_buf) cudaFree(c->tiles_buf);
+    c->tiles_buf = nullptr;
+    for (int a = 0; a < 3; ++a) c->pvar[a].clear();
     c->have_grid = false;
     c->have_state = false;
     c->npatch = 0;
@@ -131,6 +141,95 @@ void free_grid(w5ct_ctx *c) {
 PatchGeom patch_of(const w5ct_ctx *c, int p) { return c->pg[p]; }
 
 dim3 cell_grid(const w5ct_ctx *c) { return dim3((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz); }
+
+int n_variants(const w5ct_ctx *c) {
+    return c->cfg.precision == W5CT_FP64 ? num_tile_variants<double>() : num_tile_variants<float>();
+}
+
+void variant_shape(const w5ct_ctx *c, int axis, int v, int &bx, int &t2) {
+    if (c->cfg.precision == W5CT_FP64)
+        tile_shape<double>(axis, v, bx, t2);
+    else
+        tile_shape<float>(axis, v, bx, t2);
+}
+
+// the tiles of patch p (geometry g) for a sweep along `axis` in tiles of
+// bx lanes x t2 faces
+void append_tiles(std::vector<int4> &out, int p, const PatchGeom &g, int axis, int bx, int t2) {
+    const int nbx = (g.nx + bx - 1) / bx;
+    if (axis == 0 || axis == 1) {
+        for (int k = 0; k < g.nz; ++k)
+            for (int j = 0; j < (g.ny + t2 - 1) / t2; ++j)
+                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(p, i, j, k));
+    } else {
+        for (int k = 0; k < (g.nz + t2 - 1) / t2; ++k)
+            for (int j = 0; j < g.ny; ++j)
+                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(p, i, j, k));
+    }
+}
+
+// Model of a tile variant's cost per useful face: lanes and rows padded to
+// whole tiles, times the cell box's halo along the sweep axis (phase 1 is
+// about a tenth of the per-face work).  The default choice before any
+// measurement.
+double tile_model_cost(const PatchGeom &g, int axis, int bx, int t2) {
+    const int n2 = axis == 2 ? g.nz : g.ny;
+    const double pad = (double)(((g.nx + bx - 1) / bx) * bx) / g.nx * (double)(((n2 + t2 - 1) / t2) * t2) / n2;
+    const int len = axis == 0 ? bx : t2;
+    return pad * (1.0 + 0.1 * (len + 5.0) / len);
+}
+
+void default_variants(w5ct_ctx *c) {
+    const int nv = n_variants(c);
+    for (int a = 0; a < 3; ++a) {
+        c->pvar[a].assign(c->npatch, 0);
+        for (int p = 0; p < c->npatch; ++p) {
+            double best = 0;
+            for (int v = 0; v < nv; ++v) {
+                int bx, t2;
+                variant_shape(c, a, v, bx, t2);
+                const double cost = tile_model_cost(c->pg[p], a, bx, t2);
+                if (v == 0 || cost < best * (1.0 - 1e-9)) {
+                    best = cost;
+                    c->pvar[a][p] = (signed char)v;
+                }
+            }
+        }
+    }
+}
+
+// (Re)build the device tile tables from pvar: per axis, the tiles of every
+// patch grouped by variant.  Drops a captured step graph (it holds the old
+// table).
+int build_tiles(w5ct_ctx *c) {
+    std::vector<int4> all;
+    const int nv = n_variants(c);
+    for (int a = 0; a < 3; ++a) {
+        for (int v = 0; v < kMaxTileVariants; ++v) {
+            c->seg_off[a][v] = (int)all.size();
+            if (v < nv) {
+                int bx, t2;
+                variant_shape(c, a, v, bx, t2);
+                for (int p = 0; p < c->npatch; ++p)
+                    if (c->pvar[a][p] == v) append_tiles(all, p, c->pg[p], a, bx, t2);
+            }
+            c->seg_n[a][v] = (int)all.size() - c->seg_off[a][v];
+        }
+    }
+    if (all.size() > (size_t)0x7fffffff) return fail(c, W5CT_ERR_ARG, "too many sweep tiles");
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (c->tiles_buf) {
+        W5_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->tiles_buf);
+        c->tiles_buf = nullptr;
+    }
+    W5_CUDA(c, cudaMalloc(&c->tiles_buf, sizeof(int4) * all.size()));
+    W5_CUDA(c, cudaMemcpy(c->tiles_buf, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
+    return W5CT_OK;
+}
 
 int record_event(w5ct_ctx *c) {
     if (!c->timing) return W5CT_OK;
@@ -147,7 +246,7 @@ template <typename Real>
 int launch_cellb(w5ct_ctx *c) {
     const long long n = c->n;
     if (c->npatch > 1) {
-        cellb_batched_kernel<Real><<<c->ncells, dim3(32, 8), 0, c->stream>>>(
+        cellb_batched_kernel<Real><<<c->ncells, kCellBlock, 0, c->stream>>>(
             c->pg_dev, c->cells_dev, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
             plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
     } else {
@@ -166,7 +265,7 @@ int launch_speed(w5ct_ctx *c) {
     const long long n = c->n;
     W5_CUDA(c, cudaMemsetAsync(c->smax, 0, 3 * sizeof(unsigned long long) * (size_t)c->npatch, c->stream));
     if (c->npatch > 1) {
-        speed_batched_kernel<Real><<<c->ncells, dim3(32, 8), 0, c->stream>>>(
+        speed_batched_kernel<Real><<<c->ncells, kCellBlock, 0, c->stream>>>(
             c->pg_dev, c->cells_dev, plane<Real>(c->qs, n, 0), plane<Real>(c->qs, n, 1), plane<Real>(c->qs, n, 2),
             plane<Real>(c->qs, n, 3), plane<Real>(c->qs, n, 4), plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1),
             plane<Real>(c->bc, n, 2), make_phys<Real>(c->cfg), c->smax, c->flag);
@@ -199,7 +298,7 @@ int launch_dt(w5ct_ctx *c, double *dt_copy) {
 template <typename Real, int S>
 void launch_update_stage(w5ct_ctx *c, const UpdateArgs<Real> &u) {
     if (c->npatch > 1)
-        update_batched_kernel<Real, S><<<c->ncells, dim3(32, 8), 0, c->stream>>>(u, c->pg_dev, c->cells_dev, u.dt);
+        update_batched_kernel<Real, S><<<c->ncells, kCellBlock, 0, c->stream>>>(u, c->pg_dev, c->cells_dev, u.dt);
     else
         update_kernel<Real, S><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(u);
 }
@@ -262,12 +361,17 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
             for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
             int rc = record_event(c);
             if (rc) return rc;
-            if (c->npatch > 1)
-                W5_CUDA(c, launch_sweep_batched<Real>(ax, variant, a, c->pg_dev, c->tiles_dev[ax], c->ntiles[ax],
-                                                      c->stream));
-            else
+            if (c->npatch > 1) {
+                for (int v = 0; v < kMaxTileVariants; ++v) {
+                    if (!c->seg_n[ax][v]) continue;
+                    W5_CUDA(c, launch_sweep_batched<Real>(ax, variant, v, a, c->pg_dev, c->tiles_buf + c->seg_off[ax][v],
+                                                          c->seg_n[ax][v], c->stream));
+                    c->launches++;
+                }
+            } else {
                 W5_CUDA(c, launch_sweep<Real>(ax, variant, a, c->stream));
-            c->launches++;
+                c->launches++;
+            }
             rc = record_event(c);
             if (rc) return rc;
         }
@@ -396,6 +500,8 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
         if (m[0] < 1 || m[1] < 1 || m[2] < 1) return fail(c, W5CT_ERR_ARG, "patch %d: grid sizes must be >= 1", p);
         if (m[0] > 65535 * 32 || m[1] > 65535 * 8 || m[2] > 65535)
             return fail(c, W5CT_ERR_ARG, "patch %d: grid too large for the launch geometry", p);
+        if (npatch > 1 && (long long)m[0] * m[1] * m[2] > (1LL << 30))
+            return fail(c, W5CT_ERR_ARG, "patch %d: more than 2^30 cells in a batch of patches", p);
         if (!(h[0] > 0) || !(h[1] > 0) || !(h[2] > 0)) return fail(c, W5CT_ERR_ARG, "patch %d: spacings must be > 0", p);
         ntot += (long long)m[0] * m[1] * m[2];
     }
@@ -425,28 +531,14 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     c->dx = dx3[0];
     c->dy = dx3[1];
     c->dz = dx3[2];
-    // tile tables of the batched kernels: (patch, tile x, tile y, tile z)
-    std::vector<int4> tiles[3], cells;
+    // cell blocks of the batched cell-wise kernels: (patch, first cell)
+    std::vector<int4> cells;
     if (npatch > 1) {
-        const int t2x = c->cfg.precision == W5CT_FP64 ? sweep_t2<double>(0) : sweep_t2<float>(0);
-        const int t2yz = c->cfg.precision == W5CT_FP64 ? sweep_t2<double>(1) : sweep_t2<float>(1);
         for (int p = 0; p < npatch; ++p) {
             const PatchGeom &g = c->pg[p];
-            const int bx = (g.nx + 31) / 32;
-            for (int k = 0; k < g.nz; ++k)
-                for (int j = 0; j < (g.ny + t2x - 1) / t2x; ++j)
-                    for (int i = 0; i < bx; ++i) tiles[0].push_back(make_int4(p, i, j, k));
-            for (int k = 0; k < g.nz; ++k)
-                for (int j = 0; j < (g.ny + t2yz - 1) / t2yz; ++j)
-                    for (int i = 0; i < bx; ++i) tiles[1].push_back(make_int4(p, i, j, k));
-            for (int k = 0; k < (g.nz + t2yz - 1) / t2yz; ++k)
-                for (int j = 0; j < g.ny; ++j)
-                    for (int i = 0; i < bx; ++i) tiles[2].push_back(make_int4(p, i, j, k));
-            for (int k = 0; k < g.nz; ++k)
-                for (int j = 0; j < (g.ny + 7) / 8; ++j)
-                    for (int i = 0; i < bx; ++i) cells.push_back(make_int4(p, i, j, k));
+            const long long np = (long long)g.nx * g.ny * g.nz;
+            for (long long q = 0; q < np; q += kCellBlock) cells.push_back(make_int4(p, (int)q, 0, 0));
         }
-        for (int a = 0; a < 3; ++a) c->ntiles[a] = (int)tiles[a].size();
         c->ncells = (int)cells.size();
     }
     const size_t n = (size_t)c->n, rs = c->real_size;
@@ -462,11 +554,8 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     const size_t o_dt = take(8 * np), o_smax = take(24 * np), o_flag = take(4), o_hits = take(8);
     const size_t o_part = take((size_t)kRedBlocks * 8 * 8), o_red = take(64), o_pl = take(64);
     const size_t o_pg = take(sizeof(PatchGeom) * np);
-    size_t o_tiles[3] = {0, 0, 0}, o_cells = 0;
-    if (npatch > 1) {
-        for (int a = 0; a < 3; ++a) o_tiles[a] = take(sizeof(int4) * tiles[a].size());
-        o_cells = take(sizeof(int4) * cells.size());
-    }
+    size_t o_cells = 0;
+    if (npatch > 1) o_cells = take(sizeof(int4) * cells.size());
     void *slab = nullptr;
     cudaError_t e = cudaMalloc(&slab, bytes_total);
     if (e != cudaSuccess) return fail(c, W5CT_ERR_CUDA, "cudaMalloc(%zu bytes): %s", bytes_total, cudaGetErrorString(e));
@@ -497,13 +586,11 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     c->pg_dev = (PatchGeom *)(b + o_pg);
     W5_CUDA(c, cudaMemcpy(c->pg_dev, c->pg.data(), sizeof(PatchGeom) * np, cudaMemcpyHostToDevice));
     if (npatch > 1) {
-        for (int a = 0; a < 3; ++a) {
-            c->tiles_dev[a] = (int4 *)(b + o_tiles[a]);
-            W5_CUDA(c, cudaMemcpy(c->tiles_dev[a], tiles[a].data(), sizeof(int4) * tiles[a].size(),
-                                  cudaMemcpyHostToDevice));
-        }
         c->cells_dev = (int4 *)(b + o_cells);
         W5_CUDA(c, cudaMemcpy(c->cells_dev, cells.data(), sizeof(int4) * cells.size(), cudaMemcpyHostToDevice));
+        default_variants(c);
+        int rc = build_tiles(c);
+        if (rc) return rc;
     }
     W5_CUDA(c, c->cfg.precision == W5CT_FP64 ? prepare_sweeps<double>() : prepare_sweeps<float>());
     W5_CUDA(c, cudaMemsetAsync(c->flag, 0, 4, c->stream));
@@ -698,6 +785,152 @@ int w5ct_conserved_totals(w5ct_ctx *c, int patch, double out[8]) {
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
     const double dv = g.dx * g.dy * g.dz;
     for (int f = 0; f < 8; ++f) out[f] *= dv;
+    return W5CT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename Real>
+SweepArgs<Real> sweep_args(w5ct_ctx *c, int ax) {
+    const long long n = c->n;
+    SweepArgs<Real> a;
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    for (int f = 0; f < 5; ++f) a.q[f] = plane<Real>(c->qs, n, f);
+    for (int f = 0; f < 3; ++f) a.bc[f] = plane<Real>(c->bc, n, f);
+    void *Fax[3] = {c->Fx, c->Fy, c->Fz};
+    void *Sax[3] = {c->Sx, c->Sy, c->Sz};
+    for (int f = 0; f < 5; ++f) a.F[f] = plane<Real>(Fax[ax], n, f);
+    for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
+    a.K = make_phys<Real>(c->cfg);
+    a.flag = c->flag;
+    a.hits = c->hits;
+    return a;
+}
+
+// Measure every tile variant on every patch-size class and keep the fastest.
+// A class is the patches with the same (nx, n2), n2 = ny for the x- and
+// y-sweeps and nz for the z-sweep (the sizes that decide how full the tiles
+// are).  Each class is timed on its own tiles, repeated so that one launch
+// covers at least 4M faces (small classes would otherwise time launch
+// latency), `reps` launches after one untimed launch.  The sweeps only write
+// the flux buffers that every step rewrites; the floor-hit counter and the
+// non-physical flag are restored.
+template <typename Real>
+int autotune_measure(w5ct_ctx *c, int reps) {
+    int rc = launch_cellb<Real>(c);
+    if (rc) return rc;
+    unsigned long long hits0 = 0;
+    int flag0 = 0;
+    W5_CUDA(c, cudaMemcpyAsync(&hits0, c->hits, sizeof(hits0), cudaMemcpyDeviceToHost, c->stream));
+    W5_CUDA(c, cudaMemcpyAsync(&flag0, c->flag, sizeof(flag0), cudaMemcpyDeviceToHost, c->stream));
+    W5_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int nv = n_variants(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    W5_CUDA(c, cudaEventCreate(&e0));
+    W5_CUDA(c, cudaEventCreate(&e1));
+    int4 *scratch = nullptr;
+    size_t cap = 0;
+    std::vector<int4> tl;
+    rc = W5CT_OK;
+    const int variant = c->cfg.weno_variant;
+    for (int ax = 0; ax < 3 && rc == W5CT_OK; ++ax) {
+        const SweepArgs<Real> a = sweep_args<Real>(c, ax);
+        std::map<std::pair<int, int>, std::vector<int>> cls;
+        for (int p = 0; p < c->npatch; ++p)
+            cls[std::make_pair(c->pg[p].nx, ax == 2 ? c->pg[p].nz : c->pg[p].ny)].push_back(p);
+        for (auto &kv : cls) {
+            const std::vector<int> &P = kv.second;
+            long long faces = 0;
+            for (int p : P) faces += (long long)c->pg[p].nx * c->pg[p].ny * c->pg[p].nz;
+            const int R = (int)((4000000LL + faces - 1) / faces);
+            float best = 0.f;
+            int bestv = 0;
+            for (int v = 0; v < nv && rc == W5CT_OK; ++v) {
+                int bx, t2;
+                variant_shape(c, ax, v, bx, t2);
+                tl.clear();
+                for (int r = 0; r < R; ++r)
+                    for (int p : P) append_tiles(tl, p, c->pg[p], ax, bx, t2);
+                if (tl.size() > cap) {
+                    if (scratch) cudaFree(scratch);
+                    scratch = nullptr;
+                    cap = tl.size();
+                    cudaError_t e = cudaMalloc(&scratch, sizeof(int4) * cap);
+                    if (e != cudaSuccess) {
+                        rc = fail(c, W5CT_ERR_CUDA, "autotune: cudaMalloc: %s", cudaGetErrorString(e));
+                        break;
+                    }
+                }
+                cudaError_t e = cudaMemcpy(scratch, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = launch_sweep_batched<Real>(ax, variant, v, a, c->pg_dev, scratch, (int)tl.size(), c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r)
+                    e = launch_sweep_batched<Real>(ax, variant, v, a, c->pg_dev, scratch, (int)tl.size(), c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    rc = fail(c, W5CT_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+                    break;
+                }
+                if (v == 0 || ms < best) {
+                    best = ms;
+                    bestv = v;
+                }
+            }
+            for (int p : P) c->pvar[ax][p] = (signed char)bestv;
+        }
+    }
+    if (scratch) cudaFree(scratch);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    W5_CUDA(c, cudaMemcpyAsync(c->hits, &hits0, sizeof(hits0), cudaMemcpyHostToDevice, c->stream));
+    W5_CUDA(c, cudaMemcpyAsync(c->flag, &flag0, sizeof(flag0), cudaMemcpyHostToDevice, c->stream));
+    W5_CUDA(c, cudaStreamSynchronize(c->stream));
+    return build_tiles(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int w5ct_autotune(w5ct_ctx *c, int mode, int reps) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->npatch == 1) return W5CT_OK;
+    const int nv = n_variants(c);
+    if (mode >= nv || mode < W5CT_TUNE_MODEL)
+        return fail(c, W5CT_ERR_ARG, "autotune mode %d: expected -2 (model), -1 (measure) or a variant 0..%d", mode,
+                    nv - 1);
+    if (mode == W5CT_TUNE_MEASURE) {
+        if (reps < 1 || reps > 100) return fail(c, W5CT_ERR_ARG, "reps must be in 1 .. 100");
+        return c->cfg.precision == W5CT_FP64 ? autotune_measure<double>(c, reps) : autotune_measure<float>(c, reps);
+    }
+    if (mode == W5CT_TUNE_MODEL) {
+        default_variants(c);
+    } else {
+        for (int a = 0; a < 3; ++a) c->pvar[a].assign(c->npatch, (signed char)mode);
+    }
+    return build_tiles(c);
+}
+
+int w5ct_tile_variant(w5ct_ctx *c, int axis, int patch, int out[3]) {
+    if (!c || !out) return W5CT_ERR_ARG;
+    if (!c->have_grid) return fail(c, W5CT_ERR_STATE, "no grid: call w5ct_init_grid first");
+    if (axis < 0 || axis > 2) return fail(c, W5CT_ERR_ARG, "axis must be 0, 1 or 2");
+    if (check_patch(c, patch)) return W5CT_ERR_ARG;
+    const int v = c->npatch > 1 ? c->pvar[axis][patch] : 0;
+    int bx, t2;
+    variant_shape(c, axis, v, bx, t2);
+    out[0] = v;
+    out[1] = bx;
+    out[2] = t2;
     return W5CT_OK;
 }
 

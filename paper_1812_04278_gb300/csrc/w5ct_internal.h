@@ -55,6 +55,67 @@ struct SweepCfg {
     static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
 };
 
+// Tile shapes of the batched sweeps (chosen per patch and axis by the
+// autotuner).  Variant 0 is SweepCfg's tile (32 lanes); the float path also
+// has narrower tiles that waste fewer lanes on patches whose sizes are not
+// multiples of 32 or of 16: (BX, T2, faces per thread) = (16, 16, 1),
+// (8, 16, 1), (8, 8, 1).  Every variant keeps 128 registers per thread: min
+// blocks per SM = 512 / threads per block.
+constexpr int kMaxTileVariants = 4;
+
+template <int AX, typename Real, int V>
+struct TileV;
+template <int AX, typename Real>
+struct TileV<AX, Real, 0> {
+    static constexpr int T2 = SweepCfg<AX, Real>::T2, BX = 32, FPT = T2 / 8, MINB = SweepCfg<AX, Real>::MINB;
+};
+template <int AX, typename Real>
+struct TileV<AX, Real, 1> {
+    static constexpr int T2 = 16, BX = 16, FPT = 1, MINB = 2;
+};
+template <int AX, typename Real>
+struct TileV<AX, Real, 2> {
+    static constexpr int T2 = 16, BX = 8, FPT = 1, MINB = 4;
+};
+template <int AX, typename Real>
+struct TileV<AX, Real, 3> {
+    static constexpr int T2 = 8, BX = 8, FPT = 1, MINB = 8;
+};
+
+template <typename Real>
+inline int num_tile_variants() {
+    return sizeof(Real) == 4 ? kMaxTileVariants : 1;
+}
+
+// (BX, T2) of variant v along axis `axis` (host side, for the tile tables)
+template <typename Real>
+inline void tile_shape(int axis, int v, int &bx, int &t2) {
+    if (v == 0) {
+        bx = 32;
+        t2 = axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
+    } else {
+        bx = v == 1 ? 16 : 8;
+        t2 = v == 3 ? 8 : 16;
+    }
+}
+
+template <int AX, typename Real, int VAR, int V>
+struct BatchedSweep {
+    using C = TileV<AX, Real, V>;
+    using TT = SweepTile<AX, C::T2, C::BX, C::FPT>;
+    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(sweep_batched_kernel<AX, Real, VAR, C::T2, C::MINB, C::BX, C::FPT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    static cudaError_t launch(const SweepArgs<Real> &a, const PatchGeom *pgs, const int4 *tiles, int ntiles,
+                              cudaStream_t s) {
+        sweep_batched_kernel<AX, Real, VAR, C::T2, C::MINB, C::BX, C::FPT>
+            <<<ntiles, dim3(C::BX, TT::ROWS), smem, s>>>(a, pgs, tiles);
+        return cudaGetLastError();
+    }
+};
+
 // allow the dynamic shared memory of every sweep kernel of this type
 template <int AX, typename Real, int VAR>
 cudaError_t prepare_sweep_axis() {
@@ -62,8 +123,13 @@ cudaError_t prepare_sweep_axis() {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_batched_kernel<AX, Real, VAR, C::T2, C::MINB>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if ((e = BatchedSweep<AX, Real, VAR, 0>::prepare()) != cudaSuccess) return e;
+    if constexpr (sizeof(Real) == 4) {
+        if ((e = BatchedSweep<AX, Real, VAR, 1>::prepare()) != cudaSuccess) return e;
+        if ((e = BatchedSweep<AX, Real, VAR, 2>::prepare()) != cudaSuccess) return e;
+        if ((e = BatchedSweep<AX, Real, VAR, 3>::prepare()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename Real>
@@ -80,35 +146,40 @@ cudaError_t prepare_sweeps_impl() {
 // Defined in w5ct_sweep32.cu / w5ct_sweep64.cu.
 template <typename Real>
 cudaError_t prepare_sweeps();
+// Tiles `tiles` (all of tile variant tv) of the batched sweep along `axis`.
 template <typename Real>
-cudaError_t launch_sweep_batched(int axis, int variant, const SweepArgs<Real> &a, const PatchGeom *pgs,
+cudaError_t launch_sweep_batched(int axis, int variant, int tv, const SweepArgs<Real> &a, const PatchGeom *pgs,
                                  const int4 *tiles, int ntiles, cudaStream_t s);
 
-// tile heights of the sweep along each axis for this arithmetic type
+// tile heights of the single-patch sweep along each axis for this type
 template <typename Real>
 inline int sweep_t2(int axis) {
     return axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
 }
 
 template <int AX, typename Real, int VAR>
-cudaError_t launch_sweep_batched_axis(const SweepArgs<Real> &a, const PatchGeom *pgs, const int4 *tiles, int ntiles,
-                                      cudaStream_t s) {
-    using C = SweepCfg<AX, Real>;
-    sweep_batched_kernel<AX, Real, VAR, C::T2, C::MINB><<<ntiles, dim3(32, 8), C::smem, s>>>(a, pgs, tiles);
-    return cudaGetLastError();
+cudaError_t launch_sweep_batched_axis(int tv, const SweepArgs<Real> &a, const PatchGeom *pgs, const int4 *tiles,
+                                      int ntiles, cudaStream_t s) {
+    if constexpr (sizeof(Real) == 4) {
+        if (tv == 1) return BatchedSweep<AX, Real, VAR, 1>::launch(a, pgs, tiles, ntiles, s);
+        if (tv == 2) return BatchedSweep<AX, Real, VAR, 2>::launch(a, pgs, tiles, ntiles, s);
+        if (tv == 3) return BatchedSweep<AX, Real, VAR, 3>::launch(a, pgs, tiles, ntiles, s);
+    }
+    if (tv != 0) return cudaErrorInvalidValue;
+    return BatchedSweep<AX, Real, VAR, 0>::launch(a, pgs, tiles, ntiles, s);
 }
 
 template <typename Real>
-cudaError_t launch_sweep_batched_impl(int axis, int variant, const SweepArgs<Real> &a, const PatchGeom *pgs,
+cudaError_t launch_sweep_batched_impl(int axis, int variant, int tv, const SweepArgs<Real> &a, const PatchGeom *pgs,
                                       const int4 *tiles, int ntiles, cudaStream_t s) {
     if (variant == 0) {
-        if (axis == 0) return launch_sweep_batched_axis<0, Real, 0>(a, pgs, tiles, ntiles, s);
-        if (axis == 1) return launch_sweep_batched_axis<1, Real, 0>(a, pgs, tiles, ntiles, s);
-        return launch_sweep_batched_axis<2, Real, 0>(a, pgs, tiles, ntiles, s);
+        if (axis == 0) return launch_sweep_batched_axis<0, Real, 0>(tv, a, pgs, tiles, ntiles, s);
+        if (axis == 1) return launch_sweep_batched_axis<1, Real, 0>(tv, a, pgs, tiles, ntiles, s);
+        return launch_sweep_batched_axis<2, Real, 0>(tv, a, pgs, tiles, ntiles, s);
     }
-    if (axis == 0) return launch_sweep_batched_axis<0, Real, 1>(a, pgs, tiles, ntiles, s);
-    if (axis == 1) return launch_sweep_batched_axis<1, Real, 1>(a, pgs, tiles, ntiles, s);
-    return launch_sweep_batched_axis<2, Real, 1>(a, pgs, tiles, ntiles, s);
+    if (axis == 0) return launch_sweep_batched_axis<0, Real, 1>(tv, a, pgs, tiles, ntiles, s);
+    if (axis == 1) return launch_sweep_batched_axis<1, Real, 1>(tv, a, pgs, tiles, ntiles, s);
+    return launch_sweep_batched_axis<2, Real, 1>(tv, a, pgs, tiles, ntiles, s);
 }
 
 template <int AX, typename Real, int VAR>

@@ -38,17 +38,21 @@ struct SweepArgs {
     unsigned long long *hits;
 };
 
-// Tile of one block of 32 x 8 threads: 32 lanes along x always (coalesced
-// loads and stores), T2 (a multiple of 8) faces in the second direction,
-// each thread computing T2/8 faces.
-//  x-sweep: 32 faces along x  x  T2 pencils along y
-//  y-sweep: 32 pencils along x  x  T2 faces along y
-//  z-sweep: 32 pencils along x  x  T2 faces along z
+// Tile of one block: BX lanes along x (coalesced loads and stores; every
+// tile has x fastest), T2 faces or pencils in the second direction, each
+// thread computing FPT of them (the block is BX x T2/FPT threads).
+//  x-sweep: BX faces along x  x  T2 pencils along y
+//  y-sweep: BX pencils along x  x  T2 faces along y
+//  z-sweep: BX pencils along x  x  T2 faces along z
 // The cell box adds the 2 + 3 stencil cells along the sweep axis.
-template <int AX, int T2>
+template <int AX, int T2, int BX_ = 32, int FPT_ = T2 / 8>
 struct SweepTile {
-    static_assert(T2 % 8 == 0, "tile height must be a multiple of 8");
-    static constexpr int BX = 32;
+    static_assert(T2 % FPT_ == 0, "faces per thread must divide the tile height");
+    static constexpr int BX = BX_;
+    static constexpr int FPT = FPT_;                 // faces per thread
+    static constexpr int ROWS = T2 / FPT_;           // thread rows of the block
+    static constexpr int NT = BX * ROWS;
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps per block");
     static constexpr int BY = (AX == 2) ? 1 : T2;
     static constexpr int BZ = (AX == 2) ? T2 : 1;
     static constexpr int CX = BX + (AX == 0 ? 5 : 0);
@@ -56,8 +60,6 @@ struct SweepTile {
     static constexpr int CZ = BZ + (AX == 2 ? 5 : 0);
     static constexpr int NC = CX * CY * CZ;
     static constexpr int ST = (AX == 0) ? 1 : (AX == 1) ? CX : CX * CY;
-    static constexpr int NT = 256;
-    static constexpr int FPT = T2 / 8;    // faces per thread
 };
 
 // Patch geometry: cell counts, the patch's first cell in every plane (several
@@ -71,15 +73,15 @@ struct PatchGeom {
 
 // One sweep tile (tile indices tbx, tby, tbz) of the patch described by g.
 // sm: dynamic shared memory of NCQ * NC elements.
-template <int AX, typename Real, int VAR, int T2>
+template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8>
 __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
                                            Real *sm) {
-    using TT = SweepTile<AX, T2>;
+    using TT = SweepTile<AX, T2, BX, FPT>;
     const int nx = pg.nx, ny = pg.ny, nz = pg.nz;
     const size_t off = (size_t)pg.off;
     const int x0 = tbx * TT::BX, y0 = tby * TT::BY, z0 = tbz * TT::BZ;
     const int ox = x0 - (AX == 0 ? 2 : 0), oy = y0 - (AX == 1 ? 2 : 0), oz = z0 - (AX == 2 ? 2 : 0);
-    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int tid = threadIdx.x + TT::BX * threadIdx.y;
 
     // phase 1: per-cell primitives, flux and speeds of the cell box
     bool bad = false, hit = false;
@@ -95,14 +97,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const Patch
     if (bad) atomicOr(a.flag, 1);
     if (a.K.floors) {
         const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (threadIdx.x == 0 && m) atomicAdd(a.hits, (unsigned long long)__popc(m));
+        if ((tid & 31) == 0 && m) atomicAdd(a.hits, (unsigned long long)__popc(m));
     }
     __syncthreads();
 
-    // phase 2: T2/8 interfaces per thread
+    // phase 2: FPT interfaces per thread
 #pragma unroll 1
     for (int r = 0; r < TT::FPT; ++r) {
-        const int t2 = threadIdx.y + 8 * r;
+        const int t2 = threadIdx.y + TT::ROWS * r;
         const int bx = threadIdx.x;
         const int by = (AX == 2) ? 0 : t2;
         const int bz = (AX == 2) ? t2 : 0;
@@ -134,14 +136,15 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
     sweep_tile<AX, Real, VAR, T2>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<Real *>(w5ct_smem));
 }
 
-// Several patches: block b computes tile tiles[b] = (patch, tbx, tby, tbz).
-template <int AX, typename Real, int VAR, int T2, int MINB>
-__global__ void __launch_bounds__(256, MINB) sweep_batched_kernel(SweepArgs<Real> a, const PatchGeom *__restrict__ pgs,
-                                                                  const int4 *__restrict__ tiles) {
+// Several patches: block b computes tile tiles[b] = (patch, tbx, tby, tbz)
+// of shape SweepTile<AX, T2, BX, FPT>.
+template <int AX, typename Real, int VAR, int T2, int MINB, int BX, int FPT>
+__global__ void __launch_bounds__(SweepTile<AX, T2, BX, FPT>::NT, MINB)
+    sweep_batched_kernel(SweepArgs<Real> a, const PatchGeom *__restrict__ pgs, const int4 *__restrict__ tiles) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     const int4 t = tiles[blockIdx.x];
     const PatchGeom pg = pgs[t.x];
-    sweep_tile<AX, Real, VAR, T2>(a, pg, t.y, t.z, t.w, reinterpret_cast<Real *>(w5ct_smem));
+    sweep_tile<AX, Real, VAR, T2, BX, FPT>(a, pg, t.y, t.z, t.w, reinterpret_cast<Real *>(w5ct_smem));
 }
 
 // ======================================================================
@@ -172,18 +175,40 @@ __global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, cons
     cellb_cell<Real>(nx, ny, nz, 0, i, j, k, bx, by, bz, Bx, By, Bz);
 }
 
-// Several patches: block b covers the 32 x 8 cells of cells[b] = (patch, bx, by, k).
+// Cell blocks of the batched cell-wise kernels: block b of 256 threads takes
+// the cells cells[b].y .. cells[b].y + 255 of patch cells[b].x, counted in
+// storage order (x fastest) and clipped to the patch, so that every block
+// but the last of a patch is full whatever the patch's sizes.
+constexpr int kCellBlock = 256;
+
+struct CellIdx {
+    int i, j, k;
+    bool ok;
+};
+
+__device__ __forceinline__ CellIdx cell_of_block(const int4 &t, const PatchGeom &pg) {
+    const int idx = t.y + (int)threadIdx.x;
+    CellIdx c;
+    c.ok = idx < pg.nx * pg.ny * pg.nz;
+    const int row = idx / pg.nx;
+    c.i = idx - row * pg.nx;
+    c.k = row / pg.ny;
+    c.j = row - c.k * pg.ny;
+    return c;
+}
+
 template <typename Real>
-__global__ void __launch_bounds__(256) cellb_batched_kernel(const PatchGeom *__restrict__ pgs,
-                                                            const int4 *__restrict__ cells, const Real *__restrict__ bx,
-                                                            const Real *__restrict__ by, const Real *__restrict__ bz,
-                                                            Real *__restrict__ Bx, Real *__restrict__ By,
-                                                            Real *__restrict__ Bz) {
+__global__ void __launch_bounds__(kCellBlock) cellb_batched_kernel(const PatchGeom *__restrict__ pgs,
+                                                                   const int4 *__restrict__ cells,
+                                                                   const Real *__restrict__ bx,
+                                                                   const Real *__restrict__ by,
+                                                                   const Real *__restrict__ bz, Real *__restrict__ Bx,
+                                                                   Real *__restrict__ By, Real *__restrict__ Bz) {
     const int4 t = cells[blockIdx.x];
     const PatchGeom pg = pgs[t.x];
-    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
-    if (i >= pg.nx || j >= pg.ny) return;
-    cellb_cell<Real>(pg.nx, pg.ny, pg.nz, (size_t)pg.off, i, j, t.w, bx, by, bz, Bx, By, Bz);
+    const CellIdx c = cell_of_block(t, pg);
+    if (!c.ok) return;
+    cellb_cell<Real>(pg.nx, pg.ny, pg.nz, (size_t)pg.off, c.i, c.j, c.k, bx, by, bz, Bx, By, Bz);
 }
 
 // ======================================================================
@@ -363,20 +388,20 @@ __global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<R
     update_cell<Real, STAGE>(a, ug, i, j, k, *a.dt);
 }
 
-// Several patches: block b updates the 32 x 8 cells of cells[b] = (patch, bx,
-// by, k) with that patch's dt, dts[patch].
+// Several patches: block b updates the cells of cell block cells[b] (see
+// cell_of_block) with that patch's dt, dts[patch].
 template <typename Real, int STAGE>
-__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_batched_kernel(UpdateArgs<Real> a,
-                                                                            const PatchGeom *__restrict__ pgs,
-                                                                            const int4 *__restrict__ cells,
-                                                                            const double *__restrict__ dts) {
+__global__ void __launch_bounds__(kCellBlock, W5CT_UPD_MINB) update_batched_kernel(UpdateArgs<Real> a,
+                                                                                   const PatchGeom *__restrict__ pgs,
+                                                                                   const int4 *__restrict__ cells,
+                                                                                   const double *__restrict__ dts) {
     const int4 t = cells[blockIdx.x];
     const PatchGeom pg = pgs[t.x];
-    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
-    if (i >= pg.nx || j >= pg.ny) return;
+    const CellIdx c = cell_of_block(t, pg);
+    if (!c.ok) return;
     const UpdGeom<Real> ug = {pg.nx, pg.ny, pg.nz, (size_t)pg.off, (Real)pg.rdx, (Real)pg.rdy, (Real)pg.rdz,
                               pg.rdx, pg.rdy, pg.rdz};
-    update_cell<Real, STAGE>(a, ug, i, j, t.w, dts[t.x]);
+    update_cell<Real, STAGE>(a, ug, c.i, c.j, c.k, dts[t.x]);
 }
 
 // ======================================================================
@@ -454,23 +479,24 @@ __global__ void __launch_bounds__(kRedThreads) speed_kernel(long long n, int nx,
     }
 }
 
-// Several patches: block b covers the 32 x 8 cells of cells[b] = (patch, bx,
-// by, k); the maxima of patch p go to smax[3 p .. 3 p + 2] (zeroed before).
+// Several patches: block b covers the cells of cell block cells[b] (see
+// cell_of_block); the maxima of patch p go to smax[3 p .. 3 p + 2] (zeroed
+// before).
 template <typename Real>
-__global__ void __launch_bounds__(256) speed_batched_kernel(const PatchGeom *__restrict__ pgs,
-                                                            const int4 *__restrict__ cells, const Real *q0,
-                                                            const Real *q1, const Real *q2, const Real *q3,
-                                                            const Real *q4, const Real *B0, const Real *B1,
-                                                            const Real *B2, Phys<Real> K, unsigned long long *smax,
-                                                            int *flag) {
+__global__ void __launch_bounds__(kCellBlock) speed_batched_kernel(const PatchGeom *__restrict__ pgs,
+                                                                   const int4 *__restrict__ cells, const Real *q0,
+                                                                   const Real *q1, const Real *q2, const Real *q3,
+                                                                   const Real *q4, const Real *B0, const Real *B1,
+                                                                   const Real *B2, Phys<Real> K,
+                                                                   unsigned long long *smax, int *flag) {
     const int4 t = cells[blockIdx.x];
     const PatchGeom pg = pgs[t.x];
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    const int i = t.y * 32 + threadIdx.x, j = t.z * 8 + threadIdx.y;
+    const int tid = threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
     bool bad = false;
-    if (i < pg.nx && j < pg.ny) {
-        const size_t p = (size_t)pg.off + (size_t)i + (size_t)pg.nx * ((size_t)j + (size_t)pg.ny * (size_t)t.w);
+    if (t.y + tid < pg.nx * pg.ny * pg.nz) {
+        // storage order: the block's cells are consecutive in the patch
+        const size_t p = (size_t)pg.off + (size_t)t.y + (size_t)tid;
         cell_speeds<Real>(q0[p], q1[p], q2[p], q3[p], q4[p], B0[p], B1[p], B2[p], K, v, bad);
     }
     if (bad) atomicOr(flag, 1);

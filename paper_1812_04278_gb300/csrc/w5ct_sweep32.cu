@@ -15,9 +15,9 @@ cudaError_t prepare_sweeps<float>() {
 }
 
 template <>
-cudaError_t launch_sweep_batched<float>(int axis, int variant, const SweepArgs<float> &a, const PatchGeom *pgs,
-                                       const int4 *tiles, int ntiles, cudaStream_t s) {
-    return launch_sweep_batched_impl<float>(axis, variant, a, pgs, tiles, ntiles, s);
+cudaError_t launch_sweep_batched<float>(int axis, int variant, int tv, const SweepArgs<float> &a, const PatchGeom *pgs,
+                                     const int4 *tiles, int ntiles, cudaStream_t s) {
+    return launch_sweep_batched_impl<float>(axis, variant, tv, a, pgs, tiles, ntiles, s);
 }
 
 }  // namespace w5ct

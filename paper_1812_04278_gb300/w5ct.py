@@ -41,7 +41,10 @@ EXPORTED = [
     "w5ct_max_signal_speed", "w5ct_cfl_dt", "w5ct_div_b_norm", "w5ct_conserved_totals",
     "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
     "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc", "w5ct_step_graph",
+    "w5ct_autotune", "w5ct_tile_variant",
 ]
+W5CT_TUNE_MEASURE = -1
+W5CT_TUNE_MODEL = -2
 W5CT_NOALLOC_MAX_CELLS = 134217728
 
 
@@ -65,6 +68,8 @@ _sig = {
     "w5ct_step_dev": [_VP, _VP],
     "w5ct_step_cfl": [_VP, _VP],
     "w5ct_step_graph": [_VP, c_int],
+    "w5ct_autotune": [_VP, c_int, c_int],
+    "w5ct_tile_variant": [_VP, c_int, c_int, POINTER(c_int)],
     "w5ct_max_signal_speed": [_VP, c_int, _DP],
     "w5ct_cfl_dt": [_VP, _DP],
     "w5ct_div_b_norm": [_VP, c_int, _DP, _DP],
@@ -173,6 +178,17 @@ def w5ct_step_cfl(ctx, dt_dev_out=None):
 
 def w5ct_step_graph(ctx, nsteps: int):
     _check(_lib.w5ct_step_graph(ctx, int(nsteps)), "w5ct_step_graph", ctx)
+
+
+def w5ct_autotune(ctx, mode: int = W5CT_TUNE_MEASURE, reps: int = 3):
+    _check(_lib.w5ct_autotune(ctx, int(mode), int(reps)), "w5ct_autotune", ctx)
+
+
+def w5ct_tile_variant(ctx, axis: int, patch: int):
+    """(variant, BX, T2) of the tiles sweeping `patch` along `axis`."""
+    out = (c_int * 3)()
+    _check(_lib.w5ct_tile_variant(ctx, int(axis), int(patch), out), "w5ct_tile_variant", ctx)
+    return tuple(out[:])
 
 
 def w5ct_max_signal_speed(ctx, patch: int = 0) -> np.ndarray:
@@ -377,6 +393,17 @@ class Batch:
 
     def step_graph(self, nsteps):
         w5ct_step_graph(self.ctx, nsteps)
+
+    def autotune(self, mode=W5CT_TUNE_MEASURE, reps=3):
+        w5ct_autotune(self.ctx, mode, reps)
+
+    def tile_variants(self):
+        """Number of patches per (axis, variant)."""
+        out = np.zeros((3, 4), dtype=np.int64)
+        for a in range(3):
+            for p in range(self.npatch):
+                out[a, w5ct_tile_variant(self.ctx, a, p)[0]] += 1
+        return out
 
     def max_signal_speed(self, p):
         return w5ct_max_signal_speed(self.ctx, p)

@@ -167,3 +167,62 @@ def test_batch_rejects_bad_patch_index(env):
         W.w5ct_max_signal_speed(b.ctx, 2)
     assert e.value.code == W.W5CT_ERR_ARG
     b.close()
+
+
+@pytest.fixture(scope="module")
+def single_fp32(env):
+    """Two fixed-dt FP32-bulk steps of every patch of SHAPES, one context per
+    patch (the reference of the tile-variant tests)."""
+    sts = states(env, SHAPES, 700)
+    dt = 0.2 * min(1.0 / n for sh in SHAPES for n in sh)
+    out = []
+    for p, sh in enumerate(SHAPES):
+        s = make_single(env, sh, sts[p], 1, 1)
+        s.step(dt)
+        s.step(dt)
+        out.append(s.get_state())
+        s.close()
+    return sts, dt, out
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, -2, -1])
+def test_tile_variants_do_not_change_results(env, single_fp32, mode):
+    """Every sweep tile shape (forced, the model's choice or the measured
+    autotuner's) computes each face with the same arithmetic."""
+    W = env["W"]
+    sts, dt, ref = single_fp32
+    b = make_batch(env, SHAPES, sts, 1, 1)
+    b.autotune(mode, 2)
+    counts = b.tile_variants()
+    assert counts.sum(axis=1).tolist() == [len(SHAPES)] * 3
+    if mode >= 0:
+        assert counts[:, mode].tolist() == [len(SHAPES)] * 3
+    b.step(dt)
+    b.step(dt)
+    for p in range(len(SHAPES)):
+        assert_same(b.get_state(p), ref[p], ("mode", mode, "patch", p))
+    assert b.status() == (0, 0)
+    b.close()
+
+
+def test_tile_model_prefers_full_tiles(env):
+    W = env["W"]
+    shapes = [(64, 64, 64), (16, 16, 16), (24, 24, 24)]
+    sts = states(env, shapes, 800)
+    b = make_batch(env, shapes, sts, 1, 1)
+    assert W.w5ct_tile_variant(b.ctx, 0, 0) == (0, 32, 16)     # 64 = 2 x 32 lanes
+    assert W.w5ct_tile_variant(b.ctx, 0, 1)[1] == 16           # 16 lanes, not half of 32
+    assert W.w5ct_tile_variant(b.ctx, 0, 2)[1] == 8            # 24 = 3 x 8 lanes
+    b.close()
+
+
+def test_fp64_has_only_the_default_tile(env):
+    W = env["W"]
+    sts = states(env, SHAPES[:2], 900)
+    b = make_batch(env, SHAPES[:2], sts, 0, 1)
+    with pytest.raises(W.W5ctError) as e:
+        b.autotune(1)
+    assert e.value.code == W.W5CT_ERR_ARG
+    b.autotune(W.W5CT_TUNE_MEASURE, 1)
+    assert b.tile_variants()[:, 0].tolist() == [2, 2, 2]
+    b.close()
