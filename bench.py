@@ -156,7 +156,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_sweep32.cu", "w5ct_sweep64.cu"):
+    for f in ("w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_sweep32.cu", "w5ct_sweep64.cu"):
         h.update(open(os.path.join(ROOT, "paper_1812_04278_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -165,7 +165,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "49ce1afc02bedb52", "fp64": 106.38, "fp32": 44.97}
+SWEEP_TRAFFIC = {"src": "af6fe90e6dc31482", "fp64": 104.5, "fp32": 44.57}
 
 
 def sweep_traffic(key, zones):
