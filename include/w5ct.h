@@ -161,6 +161,54 @@ int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
  * `axis` (0, 1, 2).  Host only. */
 int w5ct_tile_variant(w5ct_ctx *ctx, int axis, int patch, int out[3]);
 
+/* Adjoint of one step (one patch): the vector-Jacobian product of the map
+ * (q^n, b^n) -> (q^{n+1}, b^{n+1}) of w5ct_step(ctx, dt) at the current state.
+ * lam_q (5 planes) = dL/dq^{n+1}, lam_b (3 planes) = dL/db^{n+1} in, lam_q_out
+ * = dL/dq^n, lam_b_out = dL/db^n out; all device pointers to doubles in the
+ * layout of w5ct_set_state, outputs distinct from the inputs.  dt is held
+ * fixed (the CFL dt's dependence on the state is not differentiated).  The
+ * stages are recomputed from the state (Sec. 2.1), then run backwards: the
+ * linear maps (flux divergence, Eq. num; EMF averages, Eqs. ox1-ox3; face
+ * update, Sec. 2.3; cell-field interpolation) by their transposes, each
+ * sweep by the Jacobian of its face function (cell recovery + Appendix A
+ * eigenvectors + LF splitting + WENO, Sec. 2.2) contracted with the flux
+ * adjoints.  At max(), |.| and the eps_B switches the derivative is that of
+ * the branch the forward step takes.  The arithmetic type of the forward
+ * path is kept (float Jacobians for FP32_BULK), accumulation is double.
+ * The state is not changed; the floor-hit counter and flag are kept.
+ * Synchronises.  W5CT_ERR_UNSUPPORTED for npatch > 1.  (No counterpart in
+ * the paper.) */
+int w5ct_adjoint_step(w5ct_ctx *ctx, double dt, const double *lam_q, const double *lam_b, double *lam_q_out,
+                      double *lam_b_out);
+
+/* L = 1/2 dV sum over the cells of |q - q*|^2 + |b - b*|^2 (five conserved
+ * and three face fields of the current state against target_cons,
+ * target_bface; dV = dx dy dz) into *value (host), and its gradient dV (q -
+ * q*), dV (b - b*) into lam_q, lam_b (device planes).  Fixed summation
+ * order.  Synchronises.  One patch. */
+int w5ct_misfit(w5ct_ctx *ctx, const double *target_cons, const double *target_bface, double *value, double *lam_q,
+                double *lam_b);
+
+/* Initial state from primitive fields and an edge vector potential (no
+ * context): b = curl A + B0 with the first-order discrete curl of Sec. 4.1
+ * (A_x at (i, j+1/2, k+1/2), A_y at (i+1/2, j, k+1/2), A_z at (i+1/2, j+1/2,
+ * k) in cell units from the centre of cell (i, j, k)), cons = (rho, rho v, E)
+ * with E from Eq. P and the cell field from the sixth-order face-to-centre
+ * interpolation of Sec. 4.14.  rho, P: 1 plane; v, A: 3 planes; cons 5,
+ * bface 3 planes out; device pointers, n3 = {nx, ny, nz}, dx3 and B0 on the
+ * host; `stream` a cudaStream_t or NULL.  Asynchronous. */
+int w5ct_ic_from_potential(const int n3[3], const double dx3[3], double gamma, const double B0[3], const double *rho,
+                           const double *v, const double *P, const double *A, double *cons, double *bface,
+                           void *stream);
+
+/* Adjoint of w5ct_ic_from_potential in (rho, v, A) with P and B0 fixed:
+ * given lam_cons (5 planes) and lam_bface (3 planes), writes lam_rho (1),
+ * lam_v (3), lam_A (3) and the total face-field adjoint lam_b (3 planes).
+ * bface is the forward output.  Device pointers.  Asynchronous. */
+int w5ct_ic_from_potential_adjoint(const int n3[3], const double dx3[3], const double *rho, const double *v,
+                                   const double *bface, const double *lam_cons, const double *lam_bface,
+                                   double *lam_rho, double *lam_v, double *lam_A, double *lam_b, void *stream);
+
 /* For patch `patch`: S_d = max over its cells of |v_d| + c_fast^d for d = x, y, z (Eq. cfl; the
  * fast speed of Eq. fast with B_n = B_d), out[3] on the host.  Synchronises.
  * FP32_BULK evaluates the speeds in float. */

@@ -12,8 +12,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libw5ct.so")
-SOURCES = ["w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_noalloc.cu"]
-HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h"]
+SOURCES = ["w5ct_adjoint64z.cu", "w5ct_adjoint64js.cu", "w5ct_adjoint32z.cu", "w5ct_adjoint32js.cu",
+           "w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_noalloc.cu"]
+HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_dual.cuh", "w5ct_adjoint.cuh"]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -21,7 +22,8 @@ CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # The float sweep (FP32-bulk arithmetic) uses the hardware approximate
 # reciprocal / square root and flushes subnormals; every double operation
 # and every other translation unit stays IEEE.
-TU_FLAGS = {"w5ct_sweep32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
+FAST_FLOAT = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+TU_FLAGS = {"w5ct_sweep32.cu": FAST_FLOAT, "w5ct_adjoint32z.cu": FAST_FLOAT, "w5ct_adjoint32js.cu": FAST_FLOAT}
 
 
 def _newest_input() -> float:

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "w5ct.h"
+#include "w5ct_adjoint.cuh"
 #include "w5ct_internal.h"
 
 using namespace w5ct;
@@ -60,6 +61,8 @@ struct w5ct_ctx {
     int seg_n[3][kMaxTileVariants] = {};
     int4 *cells_dev = nullptr;       // 256-cell blocks of every patch
     int ncells = 0;
+    // adjoint work buffers (w5ct_adjoint_step): allocated on first use
+    void *adj_slab = nullptr;
     // captured step (w5ct_step_graph)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -130,6 +133,8 @@ void free_grid(w5ct_ctx *c) {
     c->slab = nullptr;
     if (c->tiles_buf) cudaFree(c->tiles_buf);
     c->tiles_buf = nullptr;
+    if (c->adj_slab) cudaFree(c->adj_slab);
+    c->adj_slab = nullptr;
     for (int a = 0; a < 3; ++a) c->pvar[a].clear();
     c->have_grid = false;
     c->have_state = false;
@@ -304,7 +309,7 @@ void launch_update_stage(w5ct_ctx *c, const UpdateArgs<Real> &u) {
 }
 
 template <typename Real>
-int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
+int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage = 3, void *stage_store = nullptr) {
     const long long n = c->n;
     SweepArgs<Real> a;
     a.nx = c->nx;
@@ -352,6 +357,14 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
     void *Sax[3] = {c->Sx, c->Sy, c->Sz};
     const int variant = c->cfg.weno_variant;
     for (int s = 0; s < 4; ++s) {
+        if (stage_store) {
+            // the stage state (5 + 3 planes) before stage s, for the adjoint
+            Real *dst = reinterpret_cast<Real *>(stage_store) + (size_t)s * 8 * (size_t)n;
+            W5_CUDA(c, cudaMemcpyAsync(dst, c->qs, 5 * (size_t)n * sizeof(Real), cudaMemcpyDeviceToDevice, c->stream));
+            W5_CUDA(c, cudaMemcpyAsync(dst + 5 * (size_t)n, c->bs, 3 * (size_t)n * sizeof(Real),
+                                       cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if (s > last_stage) break;
         if (!(s == 0 && cellb_done)) {
             int rc = launch_cellb<Real>(c);
             if (rc) return rc;
@@ -896,6 +909,109 @@ int autotune_measure(w5ct_ctx *c, int reps) {
     return build_tiles(c);
 }
 
+// ---------------------------------------------------------------- adjoint
+
+// Work buffers of the adjoint step, in one allocation: stage states
+// (4 x 8 planes of Real), then double planes: two sets of stage adjoints
+// (5 + 3 each), lamD (5), mu (3), lamO (3), lamF (15), lamS (6), lamBc (3),
+// face contributions (48).
+constexpr int kAdjDoublePlanes = 2 * 8 + 5 + 3 + 3 + 15 + 6 + 3 + 48;
+
+int ensure_adj(w5ct_ctx *c) {
+    if (c->adj_slab) return W5CT_OK;
+    const size_t n = (size_t)c->n;
+    const size_t bytes = align256(32 * n * c->real_size) + (size_t)kAdjDoublePlanes * n * 8;
+    W5_CUDA(c, cudaMalloc(&c->adj_slab, bytes));
+    return W5CT_OK;
+}
+
+template <typename Real>
+int adjoint_step_impl(w5ct_ctx *c, double dt, const double *lq_fin, const double *lb_fin, double *lq_out,
+                      double *lb_out) {
+    int rc = ensure_adj(c);
+    if (rc) return rc;
+    const long long nl = c->n;
+    const size_t n = (size_t)nl;
+    cudaStream_t st = c->stream;
+    Real *stage = reinterpret_cast<Real *>(c->adj_slab);
+    double *w = reinterpret_cast<double *>((char *)c->adj_slab + align256(32 * n * sizeof(Real)));
+    double *set[2] = {w, w + 8 * n};           // stage adjoints: q (5 planes) then b (3 planes)
+    double *lamD = w + 16 * n, *mu = lamD + 5 * n, *lamO = mu + 3 * n, *lamF = lamO + 3 * n;
+    double *lamS = lamF + 15 * n, *lamBc = lamS + 6 * n, *cb = lamBc + 3 * n;
+
+    unsigned long long hits0 = 0;
+    int flag0 = 0;
+    W5_CUDA(c, cudaMemcpyAsync(&hits0, c->hits, sizeof(hits0), cudaMemcpyDeviceToHost, st));
+    W5_CUDA(c, cudaMemcpyAsync(&flag0, c->flag, sizeof(flag0), cudaMemcpyDeviceToHost, st));
+    W5_CUDA(c, cudaStreamSynchronize(st));
+
+    // forward stages 0..2 from the current state, keeping the four stage states
+    fill_kernel<<<1, 32, 0, st>>>(c->dt_dev, 1, dt);
+    rc = run_step<Real>(c, c->dt_dev, false, 2, stage);
+    if (rc) return rc;
+    // the context's stage buffers back to the state (as after set_state or a step)
+    W5_CUDA(c, cudaMemcpyAsync(c->qs, stage, 5 * n * sizeof(Real), cudaMemcpyDeviceToDevice, st));
+    W5_CUDA(c, cudaMemcpyAsync(c->bs, stage + 5 * n, 3 * n * sizeof(Real), cudaMemcpyDeviceToDevice, st));
+
+    // backward through the stages
+    W5_CUDA(c, cudaMemcpyAsync(lq_out, lq_fin, 5 * n * 8, cudaMemcpyDeviceToDevice, st));
+    W5_CUDA(c, cudaMemcpyAsync(lb_out, lb_fin, 3 * n * 8, cudaMemcpyDeviceToDevice, st));
+    const double wc[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double cs[3] = {0.5, 0.5, 1.0};
+    const AdjGrid g = {c->nx, c->ny, c->nz, 1.0 / c->dx, 1.0 / c->dy, 1.0 / c->dz};
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const Phys<Real> K = make_phys<Real>(c->cfg);
+    double *next = nullptr;
+    for (int s = 3; s >= 0; --s) {
+        double *cur = set[s & 1];
+        adj_sources_kernel<<<nb, 256, 0, st>>>(nl, dt * wc[s], s < 3 ? cs[s] * dt : 0.0, lq_fin, lb_fin,
+                                               next, next ? next + 5 * n : nullptr, lamD, mu);
+        adj_curl_kernel<<<nb, 256, 0, st>>>(g, mu, lamO);
+        adj_flux_kernel<<<nb, 256, 0, st>>>(g, lamD, lamO, lamF, lamS);
+        // the stage's cell field from its stored face field
+        const Real *sq = stage + (size_t)s * 8 * n, *sb = sq + 5 * n;
+        cellb_kernel<Real><<<cell_grid(c), dim3(32, 8), 0, st>>>(c->nx, c->ny, c->nz, sb, sb + n, sb + 2 * n,
+                                                                 plane<Real>(c->bc, nl, 0), plane<Real>(c->bc, nl, 1),
+                                                                 plane<Real>(c->bc, nl, 2));
+        W5_CUDA(c, cudaMemsetAsync(cur, 0, 5 * n * 8, st));
+        W5_CUDA(c, cudaMemsetAsync(lamBc, 0, 3 * n * 8, st));
+        for (int ax = 0; ax < 3; ++ax) {
+            AdjSweepArgs<Real> aa;
+            aa.nx = c->nx;
+            aa.ny = c->ny;
+            aa.nz = c->nz;
+            for (int f = 0; f < 5; ++f) aa.q[f] = sq + (size_t)f * n;
+            for (int f = 0; f < 3; ++f) aa.bc[f] = plane<Real>(c->bc, nl, f);
+            for (int f = 0; f < 5; ++f) aa.lamF[f] = lamF + (size_t)(5 * ax + f) * n;
+            for (int f = 0; f < 2; ++f) aa.lamS[f] = lamS + (size_t)(2 * ax + f) * n;
+            aa.cb = cb;
+            aa.K = K;
+            const cudaError_t ea = c->cfg.weno_variant == W5CT_WENO_JS ? launch_adj_sweep<Real, 0>(ax, aa, st)
+                                                                       : launch_adj_sweep<Real, 1>(ax, aa, st);
+            W5_CUDA(c, ea);
+            double *q[5], *b[3];
+            for (int f = 0; f < 5; ++f) q[f] = cur + (size_t)f * n;
+            for (int f = 0; f < 3; ++f) b[f] = lamBc + (size_t)f * n;
+            if (ax == 0)
+                adj_gather_kernel<0><<<nb, 256, 0, st>>>(c->nx, c->ny, c->nz, cb, q[0], q[1], q[2], q[3], q[4], b[0], b[1], b[2]);
+            else if (ax == 1)
+                adj_gather_kernel<1><<<nb, 256, 0, st>>>(c->nx, c->ny, c->nz, cb, q[0], q[1], q[2], q[3], q[4], b[0], b[1], b[2]);
+            else
+                adj_gather_kernel<2><<<nb, 256, 0, st>>>(c->nx, c->ny, c->nz, cb, q[0], q[1], q[2], q[3], q[4], b[0], b[1], b[2]);
+            c->launches += 2;
+        }
+        // stage face-field adjoint; both added into the step's outputs
+        adj_interp_kernel<<<nb, 256, 0, st>>>(g, lamBc, cur, cur + 5 * n, lq_out, lb_out);
+        c->launches += 5;
+        W5_CUDA(c, cudaGetLastError());
+        next = cur;
+    }
+    W5_CUDA(c, cudaMemcpyAsync(c->hits, &hits0, sizeof(hits0), cudaMemcpyHostToDevice, st));
+    W5_CUDA(c, cudaMemcpyAsync(c->flag, &flag0, sizeof(flag0), cudaMemcpyHostToDevice, st));
+    W5_CUDA(c, cudaStreamSynchronize(st));
+    return W5CT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -931,6 +1047,87 @@ int w5ct_tile_variant(w5ct_ctx *c, int axis, int patch, int out[3]) {
     out[0] = v;
     out[1] = bx;
     out[2] = t2;
+    return W5CT_OK;
+}
+
+int w5ct_adjoint_step(w5ct_ctx *c, double dt, const double *lam_q, const double *lam_b, double *lam_q_out,
+                      double *lam_b_out) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->npatch != 1) return fail(c, W5CT_ERR_UNSUPPORTED, "the adjoint step takes one patch");
+    if (!(dt > 0.0) || !(dt < 1e300)) return fail(c, W5CT_ERR_ARG, "dt must be finite and > 0 (got %g)", dt);
+    if (!lam_q || !lam_b || !lam_q_out || !lam_b_out) return fail(c, W5CT_ERR_ARG, "null adjoint buffer");
+    return c->cfg.precision == W5CT_FP64 ? adjoint_step_impl<double>(c, dt, lam_q, lam_b, lam_q_out, lam_b_out)
+                                          : adjoint_step_impl<float>(c, dt, lam_q, lam_b, lam_q_out, lam_b_out);
+}
+
+int w5ct_misfit(w5ct_ctx *c, const double *target_cons, const double *target_bface, double *value, double *lam_q,
+                double *lam_b) {
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->npatch != 1) return fail(c, W5CT_ERR_UNSUPPORTED, "the misfit takes one patch");
+    if (!target_cons || !target_bface || !value || !lam_q || !lam_b) return fail(c, W5CT_ERR_ARG, "null buffer");
+    const double dV = c->dx * c->dy * c->dz;
+    misfit_partial_kernel<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->n, dV, c->q0, c->b0, target_cons,
+                                                                     target_bface, lam_q, lam_b, c->part);
+    finalize_kernel<<<1, kRedThreads, 0, c->stream>>>(c->part, kRedBlocks, 1, 1, 0u, c->red_out);
+    c->launches += 2;
+    W5_CUDA(c, cudaGetLastError());
+    W5_CUDA(c, cudaMemcpyAsync(value, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    W5_CUDA(c, cudaStreamSynchronize(c->stream));
+    return W5CT_OK;
+}
+
+static int ic_check(const int n3[3], const double dx3[3]) {
+    if (!n3 || !dx3) return W5CT_ERR_ARG;
+    if (n3[0] < 1 || n3[1] < 1 || n3[2] < 1) return W5CT_ERR_ARG;
+    if ((long long)n3[0] * n3[1] * n3[2] > (1LL << 31)) return W5CT_ERR_ARG;
+    if (!(dx3[0] > 0) || !(dx3[1] > 0) || !(dx3[2] > 0)) return W5CT_ERR_ARG;
+    return W5CT_OK;
+}
+
+int w5ct_ic_from_potential(const int n3[3], const double dx3[3], double gamma, const double B0[3], const double *rho,
+                           const double *v, const double *P, const double *A, double *cons, double *bface,
+                           void *stream) {
+    if (ic_check(n3, dx3) || !B0 || !rho || !v || !P || !A || !cons || !bface || !(gamma > 1.0)) {
+        set_global_error("w5ct_ic_from_potential: bad argument");
+        return W5CT_ERR_ARG;
+    }
+    const AdjGrid g = {n3[0], n3[1], n3[2], 1.0 / dx3[0], 1.0 / dx3[1], 1.0 / dx3[2]};
+    const long long n = (long long)n3[0] * n3[1] * n3[2];
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    ic_curl_kernel<<<nb, 256, 0, st>>>(g, A, B0[0], B0[1], B0[2], bface);
+    ic_cons_kernel<<<nb, 256, 0, st>>>(g, gamma - 1.0, rho, v, P, bface, cons);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error(cudaGetErrorString(e));
+        return W5CT_ERR_CUDA;
+    }
+    return W5CT_OK;
+}
+
+int w5ct_ic_from_potential_adjoint(const int n3[3], const double dx3[3], const double *rho, const double *v,
+                                   const double *bface, const double *lam_cons, const double *lam_bface,
+                                   double *lam_rho, double *lam_v, double *lam_A, double *lam_b, void *stream) {
+    if (ic_check(n3, dx3) || !rho || !v || !bface || !lam_cons || !lam_bface || !lam_rho || !lam_v || !lam_A ||
+        !lam_b) {
+        set_global_error("w5ct_ic_from_potential_adjoint: bad argument");
+        return W5CT_ERR_ARG;
+    }
+    const AdjGrid g = {n3[0], n3[1], n3[2], 1.0 / dx3[0], 1.0 / dx3[1], 1.0 / dx3[2]};
+    const long long n = (long long)n3[0] * n3[1] * n3[2];
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    // lam_A holds the cell-field adjoint until the last kernel overwrites it
+    ic_cons_adjoint_kernel<<<nb, 256, 0, st>>>(g, rho, v, bface, lam_cons, lam_rho, lam_v, lam_A);
+    ic_interp_adjoint_kernel<<<nb, 256, 0, st>>>(g, lam_bface, lam_A, lam_b);
+    ic_curl_adjoint_kernel<<<nb, 256, 0, st>>>(g, lam_b, lam_A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error(cudaGetErrorString(e));
+        return W5CT_ERR_CUDA;
+    }
     return W5CT_OK;
 }
 

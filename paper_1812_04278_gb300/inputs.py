@@ -399,3 +399,49 @@ def patch_state(spec, gamma=GAMMA, dB_frac=0.1, kmin=2):
     return turbulent_state(None, seed=spec["seed"], seed_b=spec["seed_b"], mach=spec["mach"], beta=spec["beta"],
                            dB_frac=dB_frac, kmin=kmin, kmax=kmax, gamma=gamma, B_dir=spec["B_dir"],
                            shape=spec["shape"])
+
+
+# --------------------------------------------------------------------------
+# parametrised initial state (the adjoint workload)
+# --------------------------------------------------------------------------
+
+
+def ic_from_potential(rho, v, P, A, B0, dx, gamma=GAMMA):
+    """Conserved state and face field from primitive fields and an edge
+    vector potential: b = curl A + B0 (first-order discrete curl, edges as in
+    curl_edges_to_faces), E from Eq. (P) with the sixth-order face -> centre
+    interpolation of Sec. 4.14."""
+    bx, by, bz = curl_edges_to_faces(A[0], A[1], A[2], dx)
+    bface = np.stack([bx + B0[0], by + B0[1], bz + B0[2]])
+    return assemble(rho, v, P, bface, gamma)
+
+
+def cpaw_overpressure(shape, amp=0.1, kint=(1, 2, 2), p0=0.1, peak=10.0, r0=0.1, rho0=1.0):
+    """Primitive fields and edge vector potential of a circularly polarised
+    Alfven wave (Sec. 4.3 set-up: rho = 1, B_par = 1, P = 0.1, v_perp =
+    B_perp = amp (sin phi, cos phi) in the wave frame) travelling along
+    k = 2 pi kint in the unit box, plus a Gaussian overpressure
+    P = p0 (1 + (peak - 1) exp(-r^2 / r0^2)) about the box centre.  The
+    transverse field comes from A = (amp/|k|) (e1 sin phi + e2 cos phi) on the
+    edges, so b = curl A + B0 is discretely divergence free.  Returns
+    (rho, v, P, A, B0)."""
+    nx, ny, nz = shape
+    khat, e1, e2 = wave_frame(kint)
+    kvec = 2.0 * np.pi * np.asarray(kint, dtype=np.float64)
+    kmag = np.linalg.norm(kvec)
+    X, Y, Z, dx = cell_centres(shape)
+    ph = kvec[0] * X + kvec[1] * Y + kvec[2] * Z
+    v = amp * (np.sin(ph)[None] * e1[:, None, None, None] + np.cos(ph)[None] * e2[:, None, None, None])
+    r2 = (X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+    P = p0 * (1.0 + (peak - 1.0) * np.exp(-r2 / r0 ** 2))
+    rho = np.full((nz, ny, nx), rho0)
+    hx, hy, hz = dx
+    # edges: A_x at (i, j+1/2, k+1/2), A_y at (i+1/2, j, k+1/2), A_z at (i+1/2, j+1/2, k) from the centre
+    shifts = [(0.0, 0.5 * hy, 0.5 * hz), (0.5 * hx, 0.0, 0.5 * hz), (0.5 * hx, 0.5 * hy, 0.0)]
+    A = np.empty((3, nz, ny, nx))
+    for c, (sx, sy, sz) in enumerate(shifts):
+        phe = kvec[0] * (X + sx) + kvec[1] * (Y + sy) + kvec[2] * (Z + sz)
+        a = (amp / kmag) * (np.sin(phe) * e1[c] + np.cos(phe) * e2[c])
+        A[c] = a
+    B0 = tuple(float(x) for x in khat)
+    return rho, np.ascontiguousarray(v), P, A, B0

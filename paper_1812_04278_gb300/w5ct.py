@@ -41,7 +41,8 @@ EXPORTED = [
     "w5ct_max_signal_speed", "w5ct_cfl_dt", "w5ct_div_b_norm", "w5ct_conserved_totals",
     "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
     "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc", "w5ct_step_graph",
-    "w5ct_autotune", "w5ct_tile_variant",
+    "w5ct_autotune", "w5ct_tile_variant", "w5ct_adjoint_step", "w5ct_misfit", "w5ct_ic_from_potential",
+    "w5ct_ic_from_potential_adjoint",
 ]
 W5CT_TUNE_MEASURE = -1
 W5CT_TUNE_MODEL = -2
@@ -70,6 +71,10 @@ _sig = {
     "w5ct_step_graph": [_VP, c_int],
     "w5ct_autotune": [_VP, c_int, c_int],
     "w5ct_tile_variant": [_VP, c_int, c_int, POINTER(c_int)],
+    "w5ct_adjoint_step": [_VP, c_double, _VP, _VP, _VP, _VP],
+    "w5ct_misfit": [_VP, _VP, _VP, _DP, _VP, _VP],
+    "w5ct_ic_from_potential": [POINTER(c_int), _DP, c_double, _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "w5ct_ic_from_potential_adjoint": [POINTER(c_int), _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "w5ct_max_signal_speed": [_VP, c_int, _DP],
     "w5ct_cfl_dt": [_VP, _DP],
     "w5ct_div_b_norm": [_VP, c_int, _DP, _DP],
@@ -189,6 +194,39 @@ def w5ct_tile_variant(ctx, axis: int, patch: int):
     out = (c_int * 3)()
     _check(_lib.w5ct_tile_variant(ctx, int(axis), int(patch), out), "w5ct_tile_variant", ctx)
     return tuple(out[:])
+
+
+def w5ct_adjoint_step(ctx, dt: float, lam_q, lam_b, lam_q_out, lam_b_out):
+    _check(_lib.w5ct_adjoint_step(ctx, float(dt), _addr(lam_q), _addr(lam_b), _addr(lam_q_out), _addr(lam_b_out)),
+           "w5ct_adjoint_step", ctx)
+
+
+def w5ct_misfit(ctx, target_cons, target_bface, lam_q, lam_b) -> float:
+    out = c_double()
+    _check(_lib.w5ct_misfit(ctx, _addr(target_cons), _addr(target_bface), ctypes.byref(out), _addr(lam_q),
+                            _addr(lam_b)), "w5ct_misfit", ctx)
+    return out.value
+
+
+def _n3(shape):
+    return (c_int * 3)(*[int(v) for v in shape])
+
+
+def _d3(vals):
+    return (c_double * 3)(*[float(v) for v in vals])
+
+
+def w5ct_ic_from_potential(shape, dx, gamma, B0, rho, v, P, A, cons, bface, stream=None):
+    _check(_lib.w5ct_ic_from_potential(_n3(shape), _d3(dx), float(gamma), _d3(B0), _addr(rho), _addr(v), _addr(P),
+                                       _addr(A), _addr(cons), _addr(bface), stream), "w5ct_ic_from_potential")
+
+
+def w5ct_ic_from_potential_adjoint(shape, dx, rho, v, bface, lam_cons, lam_bface, lam_rho, lam_v, lam_A, lam_b,
+                                   stream=None):
+    _check(_lib.w5ct_ic_from_potential_adjoint(_n3(shape), _d3(dx), _addr(rho), _addr(v), _addr(bface),
+                                               _addr(lam_cons), _addr(lam_bface), _addr(lam_rho), _addr(lam_v),
+                                               _addr(lam_A), _addr(lam_b), stream),
+           "w5ct_ic_from_potential_adjoint")
 
 
 def w5ct_max_signal_speed(ctx, patch: int = 0) -> np.ndarray:
