@@ -72,7 +72,7 @@ def parse_args(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-n", type=int, default=64, help="edge of the oracle's sample box (reference arm)")
-    p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave", "batched"],
+    p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave", "batched", "adjoint"],
                    help="turb: 256^3 turbulence (default); blast: blast in Mach-5 turbulence (use --n 512); "
                         "wave: the 32^3 fast eigenmode (use --n 32 --steps 20); batched: 512 uneven patches")
     p.add_argument("--err-steps", type=int, default=5, help="FP64 steps of the blast error statement")
@@ -722,6 +722,154 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_adjoint(args):
+    """Gradient of the L2 misfit after --steps steps (fixed dt = the CFL dt of
+    the initial state) with respect to the initial rho, v and edge vector
+    potential, on the n^3 oblique circularly polarised Alfven wave (amplitude
+    0.1 along (1,2,2)/3) plus a Gaussian overpressure (P x10, radius 0.1 L);
+    target: the wave without the overpressure.  FP64 and FP32-bulk: forward
+    (with per-step checkpoints) and backward times, the adjoint sweep launch
+    time, and central-difference checks of a random directional derivative
+    (h = 1e-6) on this state and on a textured copy (WENO-Z is not
+    differentiable where a field is exactly uniform)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_04278_gb300 import adjoint, build, inputs
+    build.build()
+    from paper_1812_04278_gb300 import w5ct as w5
+    n = args.n
+    shape, dx, zones = (n, n, n), (1.0 / n,) * 3, n ** 3
+    stream = torch.cuda.current_stream()
+
+    def setup(texture):
+        rho, v, P, A, B0 = inputs.cpaw_overpressure(shape)
+        P_wave = inputs.cpaw_overpressure(shape, peak=1.0)[2]
+        if texture:
+            X, Y, Z, _ = inputs.cell_centres(shape)
+            ph = np.random.default_rng(42).uniform(0, 2 * np.pi, 6)
+            tp = 2 * np.pi
+            rho = rho * (1 + texture * (np.sin(tp * X + ph[0]) + np.sin(tp * Y + ph[1]) + np.sin(tp * Z + ph[2])) / 3)
+            f = 1 + texture * (np.cos(tp * X + ph[3]) + np.cos(tp * Y + ph[4]) + np.cos(tp * Z + ph[5])) / 3
+            P, P_wave = P * f, P_wave * f
+        tc, tb = inputs.ic_from_potential(rho, v, P_wave, A, B0, dx)
+        g = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        return dict(rho=g(rho), v=g(v), P=g(P), A=g(A), B0=B0, tc=g(tc), tb=g(tb))
+
+    def solver(precision):
+        return w5.Solver(shape, dx, w5.make_config(precision=precision), stream=stream.cuda_stream)
+
+    def grad(s, pb, dt):
+        rho, v, A = (pb[k].clone().requires_grad_() for k in ("rho", "v", "A"))
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        L = adjoint.rollout_misfit(rho, v, A, s, pb["P"], pb["B0"], pb["tc"], pb["tb"], dt, args.steps)
+        e1.record(stream)
+        L.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return float(L.detach()), (rho.grad, v.grad, A.grad), e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    X, Y, Z, _ = inputs.cell_centres(shape)
+
+    def smooth_field(rng, scale):
+        f = np.zeros_like(X)
+        for _ in range(3):
+            kv = rng.integers(-2, 3, size=3)
+            f += rng.standard_normal() * np.sin(2 * np.pi * (kv[0] * X + kv[1] * Y + kv[2] * Z) + rng.uniform(0, 6.3))
+        return scale * f
+
+    def fd_check(s, pb, dt, g, seed):
+        # a smooth random direction (low Fourier modes): a pointwise random
+        # one flips |IS_0 - IS_2| of WENO-Z wherever the data are smoother
+        # than the perturbation
+        rng = np.random.default_rng(seed)
+        d = [torch.from_numpy(np.ascontiguousarray(np.stack([smooth_field(rng, sc) for _ in range(m)])
+                                                   if m > 1 else smooth_field(rng, sc))).cuda()
+             for m, sc in ((1, 0.05), (3, 0.05), (3, 0.002))]
+        gd = float(sum((gi * di).sum() for gi, di in zip(g, d)))
+        h = 1e-6
+        Lp = adjoint.rollout_value(pb["rho"] + h * d[0], pb["v"] + h * d[1], pb["A"] + h * d[2], s, pb["P"], pb["B0"],
+                                   pb["tc"], pb["tb"], dt, args.steps)
+        Lm = adjoint.rollout_value(pb["rho"] - h * d[0], pb["v"] - h * d[1], pb["A"] - h * d[2], s, pb["P"], pb["B0"],
+                                   pb["tc"], pb["tb"], dt, args.steps)
+        fd = (Lp - Lm) / (2 * h)
+        return gd, fd, abs(gd - fd) / abs(fd)
+
+    pb = setup(0.0)
+    pbt = setup(0.02)
+    out = {}
+    grads = {}
+    for prec, name in ((w5.W5CT_FP64, "fp64"), (w5.W5CT_FP32_BULK, "fp32_bulk")):
+        s = solver(prec)
+        cons = torch.empty((5, n, n, n), dtype=torch.float64, device="cuda")
+        bface = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        w5.w5ct_ic_from_potential(shape, dx, 5.0 / 3.0, pb["B0"], pb["rho"], pb["v"], pb["P"], pb["A"], cons, bface,
+                                  stream.cuda_stream)
+        s.set_state(cons, bface)
+        dt = s.cfl_dt()
+        grad(s, pb, dt)                                   # warm-up
+        L, g, ms_f, ms_b = grad(s, pb, dt)
+        grads[name] = g
+        # one adjoint step with the launch timers: the sweep-adjoint share
+        lq = torch.zeros((5, n, n, n), dtype=torch.float64, device="cuda")
+        lb = torch.zeros((3, n, n, n), dtype=torch.float64, device="cuda")
+        lq[0] = 1.0
+        s.set_state(cons, bface)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        w5.w5ct_adjoint_step(s.ctx, dt, lq, lb, torch.empty_like(lq), torch.empty_like(lb))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_adj_step = e0.elapsed_time(e1)
+        rec = {"misfit": L, "dt": dt, "forward_ms": ms_f, "backward_ms": ms_b,
+               "adjoint_ms_per_step": ms_b / args.steps, "forward_ms_per_step": ms_f / args.steps,
+               "one_adjoint_step_ms": ms_adj_step,
+               "adjoint_zone_steps_per_s": zones * args.steps / (ms_b * 1e-3)}
+        if name == "fp64":
+            gd, fd, rel = fd_check(s, pb, dt, g, 11)
+            rec["fd_check"] = {"g_dot_delta": gd, "central_difference": fd, "rel_err": rel, "h": 1e-6,
+                               "state": "the workload's state (uniform rho: WENO-Z weights not differentiable there)"}
+            st = solver(prec)
+            _, gt, _, _ = grad(st, pbt, dt)
+            gd, fd, rel = fd_check(st, pbt, dt, gt, 12)
+            rec["fd_check_textured"] = {"g_dot_delta": gd, "central_difference": fd, "rel_err": rel, "h": 1e-6,
+                                        "state": "rho and P textured by 2% smooth modes"}
+            st.close()
+            sj = w5.Solver(shape, dx, w5.make_config(precision=prec, weno_variant=w5.W5CT_WENO_JS),
+                           stream=stream.cuda_stream)
+            _, gj, _, _ = grad(sj, pbt, dt)
+            gd, fd, rel = fd_check(sj, pbt, dt, gj, 13)
+            rec["fd_check_textured_js"] = {"g_dot_delta": gd, "central_difference": fd, "rel_err": rel, "h": 1e-6,
+                                           "state": "textured, WENO-JS"}
+            sj.close()
+        out[name] = rec
+        s.close()
+    rel32 = max(float((a - b).abs().max() / a.abs().max()) for a, b in zip(grads["fp64"], grads["fp32_bulk"]))
+    # directional derivatives of the two forms along one smooth direction
+    rng = np.random.default_rng(14)
+    d = [torch.from_numpy(np.ascontiguousarray(np.stack([smooth_field(rng, sc) for _ in range(m)])
+                                               if m > 1 else smooth_field(rng, sc))).cuda()
+         for m, sc in ((1, 0.05), (3, 0.05), (3, 0.002))]
+    gd64 = float(sum((g * e).sum() for g, e in zip(grads["fp64"], d)))
+    gd32 = float(sum((g * e).sum() for g, e in zip(grads["fp32_bulk"], d)))
+    value = out["fp64"]["adjoint_zone_steps_per_s"]
+    line = {
+        "metric": "adjoint zone-steps/s (gradient of a 10-step rollout misfit, backward pass)", "value": value,
+        "unit": "zone-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": out["fp64"]["adjoint_ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"periodic {n}^3 oblique circularly polarised Alfven wave (amplitude 0.1, k = 2 pi "
+                               f"(1,2,2), rho = 1, P = 0.1, B_par = 1) plus a Gaussian overpressure (P x10 peak, "
+                               f"radius 0.1); misfit to the wave without the overpressure after {args.steps} steps "
+                               f"of fixed dt (CFL 0.8 of the initial state); gradient in rho, v and the edge vector "
+                               f"potential; WENO-Z; one checkpoint per step", "zones": zones, "grid": [n, n, n]},
+        "fp64": out["fp64"], "fp32_bulk": out["fp32_bulk"], "fp32_vs_fp64_grad_max_rel": rel32,
+        "fp32_vs_fp64_directional_rel": abs(gd32 - gd64) / abs(gd64),
+        "kernel_src": kernel_source_hash(),
+    }
+    print(json.dumps(line))
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -732,6 +880,8 @@ def main(argv=None):
         run_wave(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_native(args)
 

@@ -132,13 +132,22 @@ struct M<Dual<T, N>> {
         return chain(x, s, s > T(0) ? T(0.5) / s : T(0));     // subgradient 0 at 0
     }
     static __device__ __forceinline__ D div_(const D &a, const D &b) { return a / b; }
+    // -r (r x') and -r/2 (r (r x')): no r^2 or r^3 is formed, so a large r
+    // (a tiny argument, e.g. eps + IS with IS = 0 in float) times a zero
+    // tangent stays zero instead of inf * 0
     static __device__ __forceinline__ D rcp_(const D &x) {
-        const T r = T(1) / x.v;
-        return chain(x, r, -r * r);
+        D y;
+        y.v = T(1) / x.v;
+#pragma unroll
+        for (int i = 0; i < N; ++i) y.d[i] = -y.v * (y.v * x.d[i]);
+        return y;
     }
     static __device__ __forceinline__ D rsqrt_(const D &x) {
-        const T r = T(1) / sqrt(x.v);
-        return chain(x, r, T(-0.5) * r * r * r);
+        D y;
+        y.v = T(1) / sqrt(x.v);
+#pragma unroll
+        for (int i = 0; i < N; ++i) y.d[i] = T(-0.5) * y.v * (y.v * (y.v * x.d[i]));
+        return y;
     }
     static __device__ __forceinline__ D abs_(const D &x) { return x.v >= T(0) ? x : -x; }
     static __device__ __forceinline__ D max_(const D &a, const D &b) { return a.v >= b.v ? a : b; }

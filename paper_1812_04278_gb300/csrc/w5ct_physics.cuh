@@ -230,8 +230,10 @@ __device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) 
             a1 = Real(6) * m::rcp_(s1 * s1);
             a2 = Real(3) * m::rcp_(s2 * s2);
         } else {
+            // tau / s_k as quotients (no 1/s_k^2 in the derivative: s_k can
+            // be eps_Z alone where a field is uniform)
             const Real tau = m::abs_(IS0 - IS2);
-            Real r0 = tau * m::rcp_(s0), r1 = tau * m::rcp_(s1), r2 = tau * m::rcp_(s2);
+            Real r0 = m::div_(tau, s0), r1 = m::div_(tau, s1), r2 = m::div_(tau, s2);
             if constexpr (float_based<Real>) {
                 r0 = m::min_(r0, Real(1.0e18));
                 r1 = m::min_(r1, Real(1.0e18));
