@@ -445,3 +445,69 @@ def cpaw_overpressure(shape, amp=0.1, kint=(1, 2, 2), p0=0.1, peak=10.0, r0=0.1,
         A[c] = a
     B0 = tuple(float(x) for x in khat)
     return rho, np.ascontiguousarray(v), P, A, B0
+
+
+# --------------------------------------------------------------------------
+# robustness problems (Secs. 4.4, 4.5, 4.12)
+# --------------------------------------------------------------------------
+
+
+def field_loop(shape=(128, 64, 1), L=(2.0, 1.0, 1.0), A0=1e-3, rc=0.3, v=(2.0, 1.0, 0.0), rho=1.0, P=1.0,
+               gamma=GAMMA):
+    """Magnetic field loop advection (Sec. 4.12): periodic L_x x L_y box,
+    uniform rho, v, P, and b = curl (0, 0, A_z) with A_z = A0 (rc - r) for
+    r < rc (0 outside) about the box centre, on the edges (i+1/2, j+1/2);
+    cell field by the sixth-order interpolation (Sec. 4.14).  Returns
+    (cons, bface, dx)."""
+    nx, ny, nz = shape
+    dx = (L[0] / nx, L[1] / ny, L[2] / nz)
+    X, Y, Z, _ = cell_centres(shape, L)
+    r = np.sqrt((X + 0.5 * dx[0] - 0.5 * L[0]) ** 2 + (Y + 0.5 * dx[1] - 0.5 * L[1]) ** 2)
+    Az = np.where(r < rc, A0 * (rc - r), 0.0)
+    zero = np.zeros_like(Az)
+    bx, by, bz = curl_edges_to_faces(zero, zero, Az, dx)
+    bface = np.stack([bx, by, bz])
+    o = np.ones((nz, ny, nx))
+    vv = np.stack([o * v[0], o * v[1], o * v[2]])
+    cons, bface = assemble(rho * o, vv, P * o, bface, gamma)
+    return cons, bface, dx
+
+
+def magnetic_energy(bface, dx):
+    """1/2 sum of the squared face fields times the cell volume."""
+    return 0.5 * float(np.sum(bface * bface)) * dx[0] * dx[1] * dx[2]
+
+
+# Riemann problems as printed (primitive U = (rho, v_x, v_y, v_z, B_x, B_y, B_z, P)).
+_S4PI = np.sqrt(4.0 * np.pi)
+# Sec. 4.4 prints seven entries for the left state; read as (rho, v_x, v_y,
+# B_x, B_y, B_z, P) with v_z = 0 (the right state has all eight).
+RJ2A = dict(left=(1.08, 1.2, 0.01, 0.0, 2.0 / _S4PI, 3.6 / _S4PI, 2.0 / _S4PI, 0.95),
+            right=(1.0, 0.0, 0.0, 0.0, 2.0 / _S4PI, 4.0 / _S4PI, 2.0 / _S4PI, 1.0), gamma=5.0 / 3.0, t_end=0.2)
+# Sec. 4.5, as printed (both densities 0.125), gamma = 2.
+BRIO_WU = dict(left=(0.125, 0.0, 0.0, 0.0, 0.75, 1.0, 0.0, 1.0),
+               right=(0.125, 0.0, 0.0, 0.0, 0.75, -1.0, 0.0, 0.1), gamma=2.0, t_end=0.08)
+
+
+def shock_tube(problem, n, transverse=(4, 4)):
+    """Riemann problem along x on a periodic box of length 2 (n cells along
+    x, `transverse` cells in y and z, unit cross-section): the left state on
+    [0, 0.5) and [1.5, 2), the right state on [0.5, 1.5), so that the
+    interface at x = 0.5 is the printed problem and the one at 1.5 its
+    reverse; until t_end their waves stay apart.  B_x is the same on both
+    sides, so the face field is divergence free.  Returns (cons, bface, dx,
+    gamma)."""
+    ny, nz = transverse
+    shape = (n, ny, nz)
+    L = (2.0, 1.0, 1.0)
+    dx = (L[0] / n, L[1] / ny, L[2] / nz)
+    X, _, _, _ = cell_centres(shape, L)
+    left = (X < 0.5) | (X >= 1.5)
+    UL, UR = np.asarray(problem["left"]), np.asarray(problem["right"])
+    U = np.where(left[None], UL[:, None, None, None], UR[:, None, None, None])
+    rho, v, Bc, P = U[0], U[1:4], U[4:7], U[7]
+    # fields vary along x only: b_y, b_z on their faces equal the cell values,
+    # b_x is uniform
+    bface = np.stack([np.full_like(rho, UL[4]), Bc[1], Bc[2]])
+    cons, bface = assemble(rho, v, P, bface, problem["gamma"], Bc=Bc)
+    return cons, bface, dx, problem["gamma"]

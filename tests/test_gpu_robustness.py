@@ -1,0 +1,151 @@
+"""Robustness problems through the C ABI (Secs. 4.4, 4.5, 4.11, 4.12).
+
+* Riemann problems: FP64 steps equal the oracle's to 1e-12 along the
+  trajectory (each step from identical input), including the degenerate
+  transverse field of the Brio-Wu problem (B_t = 0 at the interface, where
+  Appendix A's beta vectors take their fallback); both forms reach the
+  paper's end times without a non-physical state and without floors.
+* Field loop: the GPU keeps the oracle's magnetic-energy history and more
+  than 90% of the energy at 128 x 64 (Sec. 4.12).
+* Square advection (Sec. 4.11): WENO-Z has the smaller L1 error than WENO5,
+  as the paper reports.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1812_04278_gb300 import build
+    build.build()
+    from paper_1812_04278_gb300 import inputs, w5ct
+    oracle.build()
+    return dict(torch=torch, O=oracle, I=inputs, W=w5ct)
+
+
+def gpu_solver(env, shape, dx, precision=0, variant=1, gamma=5.0 / 3.0):
+    W, torch = env["W"], env["torch"]
+    return W.Solver(shape, dx, W.make_config(precision=precision, weno_variant=variant, gamma=gamma),
+                    stream=torch.cuda.current_stream().cuda_stream)
+
+
+def run_to(s, t_end):
+    t, n = 0.0, 0
+    while t < t_end - 1e-12:
+        dt = min(s.cfl_dt(), t_end - t)
+        s.step(dt)
+        t += dt
+        n += 1
+    return n
+
+
+@pytest.mark.parametrize("name", ["RJ2A", "BRIO_WU"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_riemann_steps_match_oracle(env, name, variant):
+    I, O = env["I"], env["O"]
+    prob = getattr(I, name)
+    cons, bface, dx, gamma = I.shock_tube(prob, 96, transverse=(2, 3))
+    shape = (96, 2, 3)
+    s = gpu_solver(env, shape, dx, 0, variant, gamma)
+    o = O.Oracle(shape, dx, O.make_config(gamma=gamma, weno_variant=variant))
+    s.set_state(cons, bface)
+    for k in range(12):
+        c, b, _ = s.get_state()
+        o.set_state(c, b)
+        dt = o.cfl_dt()
+        s.step(dt)
+        o.step(dt)
+        gc, gb, _ = s.get_state()
+        oc, ob, _ = o.get_state()
+        S = max(np.abs(oc).max(), np.abs(ob).max())
+        err = max(np.abs(gc - oc).max(), np.abs(gb - ob).max()) / S
+        assert err <= TOL64, (name, k, err)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["RJ2A", "BRIO_WU"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_riemann_problems_reach_end_time(env, name, precision):
+    I = env["I"]
+    prob = getattr(I, name)
+    cons, bface, dx, gamma = I.shock_tube(prob, 256, transverse=(4, 4))
+    s = gpu_solver(env, (256, 4, 4), dx, precision, 1, gamma)
+    s.set_state(cons, bface)
+    tot0 = s.conserved_totals()
+    run_to(s, prob["t_end"])
+    assert s.status() == (0, 0)
+    c, b, _ = s.get_state()
+    assert np.isfinite(c).all() and c[0].min() > 0
+    scale = np.abs(cons).sum() * np.prod(dx)
+    # FP32-bulk differences the face fluxes in float: the totals telescope
+    # to float rounding (the FP64 accumulation keeps them from drifting)
+    tol = 1e-13 if precision == 0 else 1e-8
+    assert np.abs(s.conserved_totals() - tot0).max() <= tol * scale
+    assert s.div_b_norm()[0] < 1e-12
+    s.close()
+
+
+def field_loop_energy(s, I, bface0, dx, marks):
+    E0 = I.magnetic_energy(bface0, dx)
+    out, t = [], 0.0
+    for m in marks:
+        while t < m - 1e-12:
+            dt = min(s.cfl_dt(), m - t)
+            s.step(dt)
+            t += dt
+        out.append(I.magnetic_energy(s.get_state()[1], dx) / E0)
+    return out
+
+
+def test_field_loop_matches_oracle_and_keeps_its_energy(env):
+    I, O = env["I"], env["O"]
+    shape = (64, 32, 1)
+    cons, bface, dx = I.field_loop(shape)
+    s = gpu_solver(env, shape, dx, 0, 0)
+    s.set_state(cons, bface)
+    Eg = field_loop_energy(s, I, bface, dx, (1.0, 2.0))
+    o = O.Oracle(shape, dx, O.make_config(weno_variant=O.WENO_JS))
+    o.set_state(cons, bface)
+    Eo, t = [], 0.0
+    for m in (1.0, 2.0):
+        while t < m - 1e-12:
+            dt = min(o.cfl_dt(), m - t)
+            o.step(dt)
+            t += dt
+        Eo.append(I.magnetic_energy(o.get_state()[1], dx) / I.magnetic_energy(bface, dx))
+    assert np.allclose(Eg, Eo, rtol=1e-9, atol=0), (Eg, Eo)
+    s.close()
+    shape = (128, 64, 1)
+    cons, bface, dx = I.field_loop(shape)
+    s = gpu_solver(env, shape, dx, 0, 0)
+    s.set_state(cons, bface)
+    E = field_loop_energy(s, I, bface, dx, (0.5, 1.0, 1.5, 2.0))
+    assert E[-1] > 0.90 and all(a >= b for a, b in zip(E, E[1:])), E
+    assert s.div_b_norm()[0] < 1e-12
+    s.close()
+
+
+def test_square_advection_weno_z_beats_weno5(env):
+    I = env["I"]
+    n = 64
+    shape = (n, n, 1)
+    X, Y, _, dx = I.cell_centres(shape)
+    rho = np.where((np.abs(X - 0.5) < 0.25) & (np.abs(Y - 0.5) < 0.25), 4.0, 1.0)
+    o1 = np.ones_like(rho)
+    c0, b0 = I.assemble(rho, np.stack([100 * o1, 50 * o1, 0 * o1]), 2.4 * o1, np.zeros((3,) + rho.shape))
+    L1 = []
+    for variant in (0, 1):
+        s = gpu_solver(env, shape, dx, 0, variant)
+        s.set_state(c0, b0)
+        run_to(s, 0.2)                 # (100, 50) x 0.2 is a whole number of boxes: exact solution = rho
+        L1.append(np.abs(s.get_state()[0][0] - rho).mean())
+        s.close()
+    assert L1[1] < 0.9 * L1[0], L1
