@@ -616,6 +616,14 @@ def run_batched(args):
     b32.autotune(w5.W5CT_TUNE_MEASURE, 3)
     tune_s = time.perf_counter() - t0
     tiles_tuned = b32.tile_variants().tolist()
+    schedule = b32.schedule()
+    # the other schedule, for the record
+    b32.set_schedule(1 - schedule)
+    reset(b32)
+    b32.step_graph(args.warmup)
+    torch.cuda.synchronize()
+    ms_other = graph_steps(b32, args.steps)
+    b32.set_schedule(schedule)
     reset(b32)
     b32.step_graph(args.warmup)
     torch.cuda.synchronize()
@@ -713,7 +721,9 @@ def run_batched(args):
         "tiles": {"variants": "0: 32x16, 1: 16x16, 2: 8x16, 3: 8x8 (lanes along x x faces)",
                   "patches_per_axis_and_variant_tuned": tiles_tuned,
                   "patches_per_axis_and_variant_model": tiles_model,
-                  "model_value": zones * args.steps / (ms_model * 1e-3), "autotune_seconds": tune_s},
+                  "model_value": zones * args.steps / (ms_model * 1e-3), "autotune_seconds": tune_s,
+                  "schedule": ["one launch per axis and variant", "persistent work queue per variant"][schedule],
+                  "other_schedule_value": zones * args.steps / (ms_other * 1e-3)},
         "unbatched_fp32": {"value": zones * nu / (msu * 1e-3), "ms_per_step": msu / nu, "steps": nu,
                            "contexts": npatch},
         "floor_hits": hits, "nonphysical": bad + bad_model, "div_b_linf": divb32,

@@ -149,13 +149,29 @@ int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
  * with the same (nx, ny) (x- and y-sweeps) or (nx, nz) (z-sweep) on the
  * current state, `reps` timed launches each, and keeps the fastest per class
  * (synchronises; needs a state; the flux buffers are overwritten, counters
- * kept).  mode = W5CT_TUNE_MODEL (the choice w5ct_init_grid makes) takes
+ * kept) and then the faster sweep schedule (w5ct_set_sweep_schedule).
+ * mode = W5CT_TUNE_MODEL (the choice w5ct_init_grid makes) takes
  * the variant with the fewest padded lanes and rows per face.  mode = v >= 0
  * forces variant v on every patch.  A captured step graph is dropped.  With
  * npatch = 1 this does nothing and returns W5CT_OK. */
 #define W5CT_TUNE_MEASURE (-1)
 #define W5CT_TUNE_MODEL (-2)
 int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
+
+/* Schedule of the batched sweeps (npatch > 1; no counterpart in the paper).
+ * 0 (the default after w5ct_init_grid): per stage, one launch per axis and
+ * tile variant over all patches' tiles.  1: per stage, one persistent launch
+ * per tile variant, as many blocks as fit on the device at once, each block
+ * taking tiles of all three axes from a device work queue (an atomically
+ * incremented counter, zeroed at the start of every step) until the list is
+ * exhausted; no block waits on another.  Every face is computed from the
+ * same source; the compiler may contract a few operations differently in
+ * the fused kernel, so results agree to rounding (not bit for bit).
+ * w5ct_autotune(W5CT_TUNE_MEASURE) also picks the faster schedule.  Changing
+ * it drops a captured step graph.  W5CT_ERR_UNSUPPORTED for schedule 1 with
+ * one patch. */
+int w5ct_set_sweep_schedule(w5ct_ctx *ctx, int schedule);
+int w5ct_sweep_schedule(w5ct_ctx *ctx, int *schedule);
 
 /* out[3] = {variant, BX, T2} of the tiles that sweep patch `patch` along
  * `axis` (0, 1, 2).  Host only. */

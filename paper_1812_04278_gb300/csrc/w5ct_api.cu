@@ -59,6 +59,10 @@ struct w5ct_ctx {
     int4 *tiles_buf = nullptr;
     int seg_off[3][kMaxTileVariants] = {};
     int seg_n[3][kMaxTileVariants] = {};
+    int schedule = 0;                // batched sweeps: 0 = one launch per axis and variant, 1 = persistent
+    int pgrid[kMaxTileVariants] = {};   // resident blocks of the persistent sweep per variant
+    int *pcounters = nullptr;        // work-queue counters: 4 stages x kMaxTileVariants
+    long long sweep_units = 0;       // axis-sweeps covered by the timed event pairs
     int4 *cells_dev = nullptr;       // 256-cell blocks of every patch
     int ncells = 0;
     // adjoint work buffers (w5ct_adjoint_step): allocated on first use
@@ -162,14 +166,15 @@ void variant_shape(const w5ct_ctx *c, int axis, int v, int &bx, int &t2) {
 // bx lanes x t2 faces
 void append_tiles(std::vector<int4> &out, int p, const PatchGeom &g, int axis, int bx, int t2) {
     const int nbx = (g.nx + bx - 1) / bx;
+    const int tag = p | (axis << kItemAxisShift);
     if (axis == 0 || axis == 1) {
         for (int k = 0; k < g.nz; ++k)
             for (int j = 0; j < (g.ny + t2 - 1) / t2; ++j)
-                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(p, i, j, k));
+                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(tag, i, j, k));
     } else {
         for (int k = 0; k < (g.nz + t2 - 1) / t2; ++k)
             for (int j = 0; j < g.ny; ++j)
-                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(p, i, j, k));
+                for (int i = 0; i < nbx; ++i) out.push_back(make_int4(tag, i, j, k));
     }
 }
 
@@ -209,8 +214,10 @@ void default_variants(w5ct_ctx *c) {
 int build_tiles(w5ct_ctx *c) {
     std::vector<int4> all;
     const int nv = n_variants(c);
-    for (int a = 0; a < 3; ++a) {
-        for (int v = 0; v < kMaxTileVariants; ++v) {
+    // variant-major, then axis: the three axes' tiles of one variant are
+    // contiguous (the work list of the persistent sweep)
+    for (int v = 0; v < kMaxTileVariants; ++v) {
+        for (int a = 0; a < 3; ++a) {
             c->seg_off[a][v] = (int)all.size();
             if (v < nv) {
                 int bx, t2;
@@ -308,6 +315,44 @@ void launch_update_stage(w5ct_ctx *c, const UpdateArgs<Real> &u) {
         update_kernel<Real, S><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(u);
 }
 
+// The three sweeps of a stage over every patch: schedule 0 launches one
+// kernel per axis and tile variant; schedule 1 one persistent kernel per
+// variant over the three axes' tiles, with the work-queue counters
+// counters[v] (zero on entry).  Each timed group is bracketed by events.
+template <typename Real>
+int launch_batched_sweeps(w5ct_ctx *c, const SweepArgs<Real> (&a3)[3], int schedule, int *counters) {
+    const int variant = c->cfg.weno_variant;
+    if (schedule == 1) {
+        int rc = record_event(c);
+        if (rc) return rc;
+        for (int v = 0; v < kMaxTileVariants; ++v) {
+            const int first = c->seg_off[0][v], last = c->seg_off[2][v] + c->seg_n[2][v];
+            if (last == first) continue;
+            W5_CUDA(c, launch_sweep_persistent<Real>(variant, v, a3, c->pg_dev, c->tiles_buf + first, last - first,
+                                                     counters + v, c->pgrid[v], c->stream));
+            c->launches++;
+        }
+        rc = record_event(c);
+        if (rc) return rc;
+        if (c->timing) c->sweep_units += 3;
+        return W5CT_OK;
+    }
+    for (int ax = 0; ax < 3; ++ax) {
+        int rc = record_event(c);
+        if (rc) return rc;
+        for (int v = 0; v < kMaxTileVariants; ++v) {
+            if (!c->seg_n[ax][v]) continue;
+            W5_CUDA(c, launch_sweep_batched<Real>(ax, variant, v, a3[ax], c->pg_dev, c->tiles_buf + c->seg_off[ax][v],
+                                                  c->seg_n[ax][v], c->stream));
+            c->launches++;
+        }
+        rc = record_event(c);
+        if (rc) return rc;
+        if (c->timing) c->sweep_units += 1;
+    }
+    return W5CT_OK;
+}
+
 template <typename Real>
 int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage = 3, void *stage_store = nullptr) {
     const long long n = c->n;
@@ -356,6 +401,8 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
     void *Fax[3] = {c->Fx, c->Fy, c->Fz};
     void *Sax[3] = {c->Sx, c->Sy, c->Sz};
     const int variant = c->cfg.weno_variant;
+    if (c->npatch > 1 && c->schedule == 1)
+        W5_CUDA(c, cudaMemsetAsync(c->pcounters, 0, 4 * kMaxTileVariants * sizeof(int), c->stream));
     for (int s = 0; s < 4; ++s) {
         if (stage_store) {
             // the stage state (5 + 3 planes) before stage s, for the adjoint
@@ -369,24 +416,26 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
             int rc = launch_cellb<Real>(c);
             if (rc) return rc;
         }
-        for (int ax = 0; ax < 3; ++ax) {
-            for (int f = 0; f < 5; ++f) a.F[f] = plane<Real>(Fax[ax], n, f);
-            for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
-            int rc = record_event(c);
+        if (c->npatch > 1) {
+            SweepArgs<Real> a3[3] = {a, a, a};
+            for (int ax = 0; ax < 3; ++ax) {
+                for (int f = 0; f < 5; ++f) a3[ax].F[f] = plane<Real>(Fax[ax], n, f);
+                for (int f = 0; f < 2; ++f) a3[ax].S[f] = plane<Real>(Sax[ax], n, f);
+            }
+            int rc = launch_batched_sweeps<Real>(c, a3, c->schedule, c->pcounters + s * kMaxTileVariants);
             if (rc) return rc;
-            if (c->npatch > 1) {
-                for (int v = 0; v < kMaxTileVariants; ++v) {
-                    if (!c->seg_n[ax][v]) continue;
-                    W5_CUDA(c, launch_sweep_batched<Real>(ax, variant, v, a, c->pg_dev, c->tiles_buf + c->seg_off[ax][v],
-                                                          c->seg_n[ax][v], c->stream));
-                    c->launches++;
-                }
-            } else {
+        } else {
+            for (int ax = 0; ax < 3; ++ax) {
+                for (int f = 0; f < 5; ++f) a.F[f] = plane<Real>(Fax[ax], n, f);
+                for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
+                int rc = record_event(c);
+                if (rc) return rc;
                 W5_CUDA(c, launch_sweep<Real>(ax, variant, a, c->stream));
                 c->launches++;
+                rc = record_event(c);
+                if (rc) return rc;
+                if (c->timing) c->sweep_units += 1;
             }
-            rc = record_event(c);
-            if (rc) return rc;
         }
         switch (s) {
             case 0: launch_update_stage<Real, 0>(c, u); break;
@@ -567,6 +616,7 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     const size_t o_dt = take(8 * np), o_smax = take(24 * np), o_flag = take(4), o_hits = take(8);
     const size_t o_part = take((size_t)kRedBlocks * 8 * 8), o_red = take(64), o_pl = take(64);
     const size_t o_pg = take(sizeof(PatchGeom) * np);
+    const size_t o_pc = take(sizeof(int) * 4 * kMaxTileVariants);
     size_t o_cells = 0;
     if (npatch > 1) o_cells = take(sizeof(int4) * cells.size());
     void *slab = nullptr;
@@ -597,6 +647,7 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     c->red_out = (double *)(b + o_red);
     c->planes = (const double **)(b + o_pl);
     c->pg_dev = (PatchGeom *)(b + o_pg);
+    c->pcounters = (int *)(b + o_pc);
     W5_CUDA(c, cudaMemcpy(c->pg_dev, c->pg.data(), sizeof(PatchGeom) * np, cudaMemcpyHostToDevice));
     if (npatch > 1) {
         c->cells_dev = (int4 *)(b + o_cells);
@@ -606,6 +657,12 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
         if (rc) return rc;
     }
     W5_CUDA(c, c->cfg.precision == W5CT_FP64 ? prepare_sweeps<double>() : prepare_sweeps<float>());
+    c->schedule = 0;
+    for (int v = 0; v < n_variants(c); ++v) {
+        const cudaError_t eg = c->cfg.precision == W5CT_FP64 ? persistent_grid<double>(c->cfg.weno_variant, v, c->pgrid[v])
+                                                             : persistent_grid<float>(c->cfg.weno_variant, v, c->pgrid[v]);
+        W5_CUDA(c, eg);
+    }
     W5_CUDA(c, cudaMemsetAsync(c->flag, 0, 4, c->stream));
     W5_CUDA(c, cudaMemsetAsync(c->hits, 0, 8, c->stream));
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -900,13 +957,46 @@ int autotune_measure(w5ct_ctx *c, int reps) {
         }
     }
     if (scratch) cudaFree(scratch);
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
+    rc = build_tiles(c);
+    if (rc) return rc;
+    // schedule: one launch per axis and variant, or one persistent launch per
+    // variant over the three axes (timed on the sweeps of a stage)
+    SweepArgs<Real> a3[3] = {sweep_args<Real>(c, 0), sweep_args<Real>(c, 1), sweep_args<Real>(c, 2)};
+    float best = 0.f;
+    const bool timing = c->timing;
+    c->timing = false;
+    for (int sc = 0; sc < 2; ++sc) {
+        float total = 0.f;
+        for (int r = 0; r <= reps; ++r) {
+            W5_CUDA(c, cudaMemsetAsync(c->pcounters, 0, 4 * kMaxTileVariants * sizeof(int), c->stream));
+            W5_CUDA(c, cudaEventRecord(e0, c->stream));
+            rc = launch_batched_sweeps<Real>(c, a3, sc, c->pcounters);
+            if (rc) break;
+            W5_CUDA(c, cudaEventRecord(e1, c->stream));
+            W5_CUDA(c, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            W5_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) total += ms;       // the first launch is untimed
+        }
+        if (rc) break;
+        if (sc == 0 || total < best) {
+            best = total;
+            c->schedule = sc;
+        }
+    }
+    c->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
     W5_CUDA(c, cudaMemcpyAsync(c->hits, &hits0, sizeof(hits0), cudaMemcpyHostToDevice, c->stream));
     W5_CUDA(c, cudaMemcpyAsync(c->flag, &flag0, sizeof(flag0), cudaMemcpyHostToDevice, c->stream));
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
-    return build_tiles(c);
+    return W5CT_OK;
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1034,6 +1124,26 @@ int w5ct_autotune(w5ct_ctx *c, int mode, int reps) {
         for (int a = 0; a < 3; ++a) c->pvar[a].assign(c->npatch, (signed char)mode);
     }
     return build_tiles(c);
+}
+
+int w5ct_set_sweep_schedule(w5ct_ctx *c, int schedule) {
+    if (!c) return W5CT_ERR_ARG;
+    if (!c->have_grid) return fail(c, W5CT_ERR_STATE, "no grid: call w5ct_init_grid first");
+    if (schedule != 0 && schedule != 1) return fail(c, W5CT_ERR_ARG, "schedule must be 0 or 1");
+    if (schedule == 1 && c->npatch == 1)
+        return fail(c, W5CT_ERR_UNSUPPORTED, "the persistent sweep schedule takes a batch of patches");
+    if (c->schedule != schedule && c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->schedule = schedule;
+    return W5CT_OK;
+}
+
+int w5ct_sweep_schedule(w5ct_ctx *c, int *schedule) {
+    if (!c || !schedule) return W5CT_ERR_ARG;
+    *schedule = c->schedule;
+    return W5CT_OK;
 }
 
 int w5ct_tile_variant(w5ct_ctx *c, int axis, int patch, int out[3]) {
@@ -1199,6 +1309,7 @@ int w5ct_set_timing(w5ct_ctx *c, int enable) {
     W5_CUDA(c, cudaStreamSynchronize(c->stream));
     c->timing = enable != 0;
     c->ev_used = 0;
+    c->sweep_units = 0;
     return W5CT_OK;
 }
 
@@ -1211,7 +1322,7 @@ int w5ct_sweep_timing(w5ct_ctx *c, long long *launches, double *total_ms) {
         W5_CUDA(c, cudaEventElapsedTime(&ms, c->ev[e], c->ev[e + 1]));
         tot += ms;
     }
-    *launches = (long long)(c->ev_used / 2);
+    *launches = c->sweep_units;
     *total_ms = tot;
     return W5CT_OK;
 }

@@ -116,6 +116,82 @@ struct BatchedSweep {
     }
 };
 
+// Persistent sweep of one tile variant over the three axes: a grid of
+// resident blocks takes work items (tiles of any axis, the axis in bits 28-29
+// of item.x, the patch in bits 0-27) from a device counter with atomicAdd
+// until the list is exhausted.  Nothing waits on another block, so the
+// queue needs no spin; the counter is zeroed before the launch.  The three
+// axes' sweeps of a stage are independent (all read the stage state), so one
+// queue covers them and their tails overlap.
+template <typename Real, int VAR, int V>
+struct PersistentSweep {
+    using C0 = TileV<0, Real, V>;
+    using C1 = TileV<1, Real, V>;
+    using C2 = TileV<2, Real, V>;
+    using T0 = SweepTile<0, C0::T2, C0::BX, C0::FPT>;
+    using T1 = SweepTile<1, C1::T2, C1::BX, C1::FPT>;
+    using T2_ = SweepTile<2, C2::T2, C2::BX, C2::FPT>;
+    static_assert(T0::NT == T1::NT && T1::NT == T2_::NT && C0::BX == C1::BX && C1::BX == C2::BX,
+                  "one block shape for the three axes");
+    static constexpr int NT = T0::NT, BX = C0::BX, ROWS = T0::ROWS, MINB = C0::MINB;
+    static constexpr size_t smem0 = (size_t)T0::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem1 = (size_t)T1::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem2 = (size_t)T2_::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem = smem0 > smem1 ? (smem0 > smem2 ? smem0 : smem2) : (smem1 > smem2 ? smem1 : smem2);
+};
+
+template <typename Real, int VAR, int V>
+__global__ void __launch_bounds__(PersistentSweep<Real, VAR, V>::NT, PersistentSweep<Real, VAR, V>::MINB)
+    sweep_persistent_kernel(SweepArgs<Real> a0, SweepArgs<Real> a1, SweepArgs<Real> a2,
+                            const PatchGeom *__restrict__ pgs, const int4 *__restrict__ items, int nitems,
+                            int *counter) {
+    using P = PersistentSweep<Real, VAR, V>;
+    extern __shared__ __align__(16) unsigned char w5ct_smem[];
+    __shared__ int s_item;
+    Real *sm = reinterpret_cast<Real *>(w5ct_smem);
+    for (;;) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;           // the same value in every thread of the block
+        const int4 t = items[it];
+        const int ax = t.x >> kItemAxisShift;
+        const PatchGeom pg = pgs[t.x & kItemPatchMask];
+        if (ax == 0)
+            sweep_tile<0, Real, VAR, P::C0::T2, P::BX, P::C0::FPT>(a0, pg, t.y, t.z, t.w, sm);
+        else if (ax == 1)
+            sweep_tile<1, Real, VAR, P::C1::T2, P::BX, P::C1::FPT>(a1, pg, t.y, t.z, t.w, sm);
+        else
+            sweep_tile<2, Real, VAR, P::C2::T2, P::BX, P::C2::FPT>(a2, pg, t.y, t.z, t.w, sm);
+        __syncthreads();                   // shared memory and s_item are reused
+    }
+}
+
+template <typename Real, int VAR, int V>
+struct PersistentLaunch {
+    using P = PersistentSweep<Real, VAR, V>;
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(sweep_persistent_kernel<Real, VAR, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)P::smem);
+    }
+    // resident blocks of this kernel on the whole device
+    static cudaError_t grid(int &blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_persistent_kernel<Real, VAR, V>, P::NT, P::smem);
+        blocks = sms * (per > 0 ? per : 1);
+        return e;
+    }
+    static cudaError_t launch(const SweepArgs<Real> (&a)[3], const PatchGeom *pgs, const int4 *items, int nitems,
+                              int *counter, int blocks, cudaStream_t s) {
+        sweep_persistent_kernel<Real, VAR, V><<<blocks, dim3(P::BX, P::ROWS), P::smem, s>>>(a[0], a[1], a[2], pgs, items,
+                                                                                         nitems, counter);
+        return cudaGetLastError();
+    }
+};
+
 // allow the dynamic shared memory of every sweep kernel of this type
 template <int AX, typename Real, int VAR>
 cudaError_t prepare_sweep_axis() {
@@ -128,6 +204,14 @@ cudaError_t prepare_sweep_axis() {
         if ((e = BatchedSweep<AX, Real, VAR, 1>::prepare()) != cudaSuccess) return e;
         if ((e = BatchedSweep<AX, Real, VAR, 2>::prepare()) != cudaSuccess) return e;
         if ((e = BatchedSweep<AX, Real, VAR, 3>::prepare()) != cudaSuccess) return e;
+    }
+    if constexpr (AX == 0) {
+        if ((e = PersistentLaunch<Real, VAR, 0>::prepare()) != cudaSuccess) return e;
+        if constexpr (sizeof(Real) == 4) {
+            if ((e = PersistentLaunch<Real, VAR, 1>::prepare()) != cudaSuccess) return e;
+            if ((e = PersistentLaunch<Real, VAR, 2>::prepare()) != cudaSuccess) return e;
+            if ((e = PersistentLaunch<Real, VAR, 3>::prepare()) != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -150,6 +234,37 @@ cudaError_t prepare_sweeps();
 template <typename Real>
 cudaError_t launch_sweep_batched(int axis, int variant, int tv, const SweepArgs<Real> &a, const PatchGeom *pgs,
                                  const int4 *tiles, int ntiles, cudaStream_t s);
+
+// The persistent sweep of tile variant tv over items (three axes, see
+// sweep_persistent_kernel) with `blocks` resident blocks; and that block count.
+template <typename Real>
+cudaError_t launch_sweep_persistent(int variant, int tv, const SweepArgs<Real> (&a)[3], const PatchGeom *pgs,
+                                    const int4 *items, int nitems, int *counter, int blocks, cudaStream_t s);
+template <typename Real>
+cudaError_t persistent_grid(int variant, int tv, int &blocks);
+
+template <typename Real, int VAR>
+cudaError_t launch_sweep_persistent_v(int tv, const SweepArgs<Real> (&a)[3], const PatchGeom *pgs, const int4 *items,
+                                      int nitems, int *counter, int blocks, cudaStream_t s) {
+    if constexpr (sizeof(Real) == 4) {
+        if (tv == 1) return PersistentLaunch<Real, VAR, 1>::launch(a, pgs, items, nitems, counter, blocks, s);
+        if (tv == 2) return PersistentLaunch<Real, VAR, 2>::launch(a, pgs, items, nitems, counter, blocks, s);
+        if (tv == 3) return PersistentLaunch<Real, VAR, 3>::launch(a, pgs, items, nitems, counter, blocks, s);
+    }
+    if (tv != 0) return cudaErrorInvalidValue;
+    return PersistentLaunch<Real, VAR, 0>::launch(a, pgs, items, nitems, counter, blocks, s);
+}
+
+template <typename Real, int VAR>
+cudaError_t persistent_grid_v(int tv, int &blocks) {
+    if constexpr (sizeof(Real) == 4) {
+        if (tv == 1) return PersistentLaunch<Real, VAR, 1>::grid(blocks);
+        if (tv == 2) return PersistentLaunch<Real, VAR, 2>::grid(blocks);
+        if (tv == 3) return PersistentLaunch<Real, VAR, 3>::grid(blocks);
+    }
+    if (tv != 0) return cudaErrorInvalidValue;
+    return PersistentLaunch<Real, VAR, 0>::grid(blocks);
+}
 
 // tile heights of the single-patch sweep along each axis for this type
 template <typename Real>

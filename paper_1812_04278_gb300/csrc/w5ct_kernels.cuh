@@ -136,6 +136,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
     sweep_tile<AX, Real, VAR, T2>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<Real *>(w5ct_smem));
 }
 
+// Tile tables hold int4 (patch | axis << 28, tile x, tile y, tile z).
+constexpr int kItemAxisShift = 28;
+constexpr int kItemPatchMask = (1 << kItemAxisShift) - 1;
+
 // Several patches: block b computes tile tiles[b] = (patch, tbx, tby, tbz)
 // of shape SweepTile<AX, T2, BX, FPT>.
 template <int AX, typename Real, int VAR, int T2, int MINB, int BX, int FPT>
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(SweepTile<AX, T2, BX, FPT>::NT, MINB)
     sweep_batched_kernel(SweepArgs<Real> a, const PatchGeom *__restrict__ pgs, const int4 *__restrict__ tiles) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     const int4 t = tiles[blockIdx.x];
-    const PatchGeom pg = pgs[t.x];
+    const PatchGeom pg = pgs[t.x & kItemPatchMask];
     sweep_tile<AX, Real, VAR, T2, BX, FPT>(a, pg, t.y, t.z, t.w, reinterpret_cast<Real *>(w5ct_smem));
 }
 

@@ -20,4 +20,16 @@ cudaError_t launch_sweep_batched<float>(int axis, int variant, int tv, const Swe
     return launch_sweep_batched_impl<float>(axis, variant, tv, a, pgs, tiles, ntiles, s);
 }
 
+template <>
+cudaError_t launch_sweep_persistent<float>(int variant, int tv, const SweepArgs<float> (&a)[3], const PatchGeom *pgs,
+                                        const int4 *items, int nitems, int *counter, int blocks, cudaStream_t s) {
+    return variant == 0 ? launch_sweep_persistent_v<float, 0>(tv, a, pgs, items, nitems, counter, blocks, s)
+                        : launch_sweep_persistent_v<float, 1>(tv, a, pgs, items, nitems, counter, blocks, s);
+}
+
+template <>
+cudaError_t persistent_grid<float>(int variant, int tv, int &blocks) {
+    return variant == 0 ? persistent_grid_v<float, 0>(tv, blocks) : persistent_grid_v<float, 1>(tv, blocks);
+}
+
 }  // namespace w5ct

@@ -20,4 +20,16 @@ cudaError_t launch_sweep_batched<double>(int axis, int variant, int tv, const Sw
     return launch_sweep_batched_impl<double>(axis, variant, tv, a, pgs, tiles, ntiles, s);
 }
 
+template <>
+cudaError_t launch_sweep_persistent<double>(int variant, int tv, const SweepArgs<double> (&a)[3], const PatchGeom *pgs,
+                                        const int4 *items, int nitems, int *counter, int blocks, cudaStream_t s) {
+    return variant == 0 ? launch_sweep_persistent_v<double, 0>(tv, a, pgs, items, nitems, counter, blocks, s)
+                        : launch_sweep_persistent_v<double, 1>(tv, a, pgs, items, nitems, counter, blocks, s);
+}
+
+template <>
+cudaError_t persistent_grid<double>(int variant, int tv, int &blocks) {
+    return variant == 0 ? persistent_grid_v<double, 0>(tv, blocks) : persistent_grid_v<double, 1>(tv, blocks);
+}
+
 }  // namespace w5ct

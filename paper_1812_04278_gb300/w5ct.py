@@ -42,7 +42,7 @@ EXPORTED = [
     "w5ct_status", "w5ct_synchronize", "w5ct_set_timing", "w5ct_sweep_timing",
     "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc", "w5ct_step_graph",
     "w5ct_autotune", "w5ct_tile_variant", "w5ct_adjoint_step", "w5ct_misfit", "w5ct_ic_from_potential",
-    "w5ct_ic_from_potential_adjoint",
+    "w5ct_ic_from_potential_adjoint", "w5ct_set_sweep_schedule", "w5ct_sweep_schedule",
 ]
 W5CT_TUNE_MEASURE = -1
 W5CT_TUNE_MODEL = -2
@@ -72,6 +72,8 @@ _sig = {
     "w5ct_autotune": [_VP, c_int, c_int],
     "w5ct_tile_variant": [_VP, c_int, c_int, POINTER(c_int)],
     "w5ct_adjoint_step": [_VP, c_double, _VP, _VP, _VP, _VP],
+    "w5ct_set_sweep_schedule": [_VP, c_int],
+    "w5ct_sweep_schedule": [_VP, POINTER(c_int)],
     "w5ct_misfit": [_VP, _VP, _VP, _DP, _VP, _VP],
     "w5ct_ic_from_potential": [POINTER(c_int), _DP, c_double, _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "w5ct_ic_from_potential_adjoint": [POINTER(c_int), _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -187,6 +189,16 @@ def w5ct_step_graph(ctx, nsteps: int):
 
 def w5ct_autotune(ctx, mode: int = W5CT_TUNE_MEASURE, reps: int = 3):
     _check(_lib.w5ct_autotune(ctx, int(mode), int(reps)), "w5ct_autotune", ctx)
+
+
+def w5ct_set_sweep_schedule(ctx, schedule: int):
+    _check(_lib.w5ct_set_sweep_schedule(ctx, int(schedule)), "w5ct_set_sweep_schedule", ctx)
+
+
+def w5ct_sweep_schedule(ctx) -> int:
+    out = c_int()
+    _check(_lib.w5ct_sweep_schedule(ctx, ctypes.byref(out)), "w5ct_sweep_schedule", ctx)
+    return out.value
 
 
 def w5ct_tile_variant(ctx, axis: int, patch: int):
@@ -434,6 +446,12 @@ class Batch:
 
     def autotune(self, mode=W5CT_TUNE_MEASURE, reps=3):
         w5ct_autotune(self.ctx, mode, reps)
+
+    def set_schedule(self, schedule):
+        w5ct_set_sweep_schedule(self.ctx, schedule)
+
+    def schedule(self):
+        return w5ct_sweep_schedule(self.ctx)
 
     def tile_variants(self):
         """Number of patches per (axis, variant)."""

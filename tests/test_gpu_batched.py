@@ -226,3 +226,41 @@ def test_fp64_has_only_the_default_tile(env):
     b.autotune(W.W5CT_TUNE_MEASURE, 1)
     assert b.tile_variants()[:, 0].tolist() == [2, 2, 2]
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_persistent_schedule_gives_the_same_results(env, single_fp32, precision, variant):
+    """The persistent work-queue sweep (schedule 1) computes every face from
+    the same source as one launch per axis; the compiler may contract a few
+    operations differently in the fused kernel, so the states agree to
+    rounding (1e-13 of the state scale after four steps, eager and replayed
+    from a graph, several tile variants in use)."""
+    sts = states(env, SHAPES, 1000 + 10 * precision + variant)
+    a = make_batch(env, SHAPES, sts, precision, variant)
+    b = make_batch(env, SHAPES, sts, precision, variant)
+    b.set_schedule(1)
+    assert b.schedule() == 1
+    for _ in range(2):
+        a.step_cfl()
+        b.step_cfl()
+    b.step_graph(2)
+    a.step_graph(2)
+    a.synchronize()
+    b.synchronize()
+    tol = 1e-13 if precision == 0 else 1e-5
+    for p in range(len(SHAPES)):
+        for x, y in zip(a.get_state(p), b.get_state(p)):
+            assert np.abs(x - y).max() <= tol * np.abs(x).max(), ("patch", p)
+    assert b.status()[1] == 0
+    a.close()
+    b.close()
+
+
+def test_persistent_schedule_needs_a_batch(env):
+    W, torch = env["W"], env["torch"]
+    s = W.Solver((8, 8, 8), 0.125, W.make_config(), stream=torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(W.W5ctError) as e:
+        W.w5ct_set_sweep_schedule(s.ctx, 1)
+    assert e.value.code == W.W5CT_ERR_UNSUPPORTED
+    s.close()
