@@ -10,10 +10,12 @@
 // state through the sweeps (nonlinear, per face) and the divergence, EMF
 // average and cell-field interpolation (linear).  The adjoint runs the
 // stages backwards: the linear maps by their transposes (the kernels below),
-// the sweeps by adj_sweep_kernel, which contracts the incoming flux adjoints
-// with the 7 x 48 Jacobian of each face obtained with dual numbers.
+// the sweeps by adj_face_kernel, the reverse mode of each face's function
+// (48 inputs -> 7 outputs) contracted with the incoming flux adjoints.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "w5ct_dual.cuh"
 #include "w5ct_kernels.cuh"
@@ -33,20 +35,181 @@ struct AdjSweepArgs {
     Phys<B> K;
 };
 
-// Face p (the interface between cell p and its successor along AX) reads
-// stencil cells p-2 .. p+3; its outputs are the five lab-order face fluxes
-// and the two transport fluxes.  The face function is evaluated exactly as in
-// the sweep (cell_fill + face_flux) with dual numbers of ND directions: pass
-// (s, c) seeds inputs c*ND .. c*ND+ND-1 of stencil cell s (inputs rho, m_x,
-// m_y, m_z, E, B_x, B_y, B_z), and the tangents of the outputs are
-// contracted with lam.  48/ND passes give the whole 7 x 48 Jacobian; a small
-// ND keeps the dual state in registers and the code small.
-constexpr int kAdjND = 2;
+// ---------------------------------------------------------------- reverse mode
 
+// The seven characteristic modes of Appendix A at the interface state w =
+// (rho, v_n, v_t1, v_t2, B_n, B_t1, B_t2, P) as full left and right
+// eigenvectors in the frame order (rho, m_n, m_t1, m_t2, B_t1, B_t2, E):
+// modes 0/1 fast (v -/+ c_f), 2/3 slow (v -/+ c_slow), 4/5 Alfven
+// (v -/+ c_A), 6 entropy.  The formulas (and branches) of face_flux, written
+// as whole vectors: the paired forms there are L = Lc +- Ls, R = Rc +- Rs.
+template <typename Real>
+__device__ __forceinline__ void eigen7(const Real (&w)[8], const Phys<Real> &K, Real (&L)[7][7], Real (&R)[7][7]) {
+    using m = M<Real>;
+    const Real r = w[0], vn = w[1], vt1 = w[2], vt2 = w[3], Bn = w[4], Bt1 = w[5], Bt2 = w[6], P = w[7];
+    const Real ir = m::rcp_(r);
+    const Real ca2 = Bn * Bn * ir;
+    const Real btm = Bt1 * Bt1 + Bt2 * Bt2;
+    const Real bt2 = btm * ir;
+    const Real v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    Real cs2 = K.gamma * P * ir;
+    if constexpr (float_based<Real>) cs2 = m::max_(cs2, K.cs2_rel * (v2 + ca2 + bt2));
+    Real fmc, cms, cf2, csl2;
+    speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+    const Real cf = m::sqrt_(cf2), csl = m::sqrt_(csl2), cs = m::sqrt_(cs2);
+    const Real dfs = fmc + cms;
+    Real af, as;
+    if (dfs >= K.eps_b2) {
+        const Real idf = m::rcp_(dfs);
+        af = m::sqrt_(m::max_(cms * idf, Real(0)));
+        as = m::sqrt_(m::max_(fmc * idf, Real(0)));
+    } else {
+        af = Real(1);
+        as = Real(1);
+    }
+    Real b1, b2;
+    if (btm > K.eps_b) {
+        const Real ib = m::rsqrt_(btm);
+        b1 = Bt1 * ib;
+        b2 = Bt2 * ib;
+    } else {
+        b1 = Real(0.70710678118654752440);
+        b2 = Real(0.70710678118654752440);
+    }
+    const Real sg = (Bn >= K.eps_b) ? Real(1) : Real(-1);
+    const Real sr = m::sqrt_(r);
+    const Real isr = sr * ir;
+    const Real bv = b1 * vt1 + b2 * vt2;
+    const Real Gf = af * cf * vn - as * csl * sg * bv;
+    const Real Ga = sg * (b2 * vt1 - b1 * vt2);
+    const Real Gs = as * csl * vn + af * cf * sg * bv;
+    const Real ics2 = m::rcp_(cs2);
+    const Real pre = Real(0.5) * ics2;
+    const Real tau = K.gm1 * ics2;
+    auto pair = [&](int mu, const Real (&Lc)[7], const Real (&Ls)[4], const Real (&Rc)[7], const Real (&Rs)[4]) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            L[mu][c] = Lc[c];
+            L[mu + 1][c] = Lc[c];
+            R[mu][c] = Rc[c];
+            R[mu + 1][c] = Rc[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            L[mu][c] = L[mu][c] + Ls[c];
+            L[mu + 1][c] = L[mu + 1][c] - Ls[c];
+        }
+        const int rows[4] = {1, 2, 3, 6};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            R[mu][rows[k]] = R[mu][rows[k]] + Rs[k];
+            R[mu + 1][rows[k]] = R[mu + 1][rows[k]] - Rs[k];
+        }
+    };
+    {
+        const Real k1 = -K.gm1 * af;
+        const Real Lc[7] = {pre * K.g1 * af * v2, pre * k1 * vn, pre * k1 * vt1, pre * k1 * vt2,
+                            pre * (k1 * Bt1 + sr * cs * as * b1), pre * (k1 * Bt2 + sr * cs * as * b2), pre * K.gm1 * af};
+        const Real Ls[4] = {pre * Gf, -pre * af * cf, pre * csl * as * b1 * sg, pre * csl * as * b2 * sg};
+        const Real Rc[7] = {af, af * vn, af * vt1, af * vt2, cs * as * b1 * isr, cs * as * b2 * isr,
+                            af * (Real(0.5) * v2 + cf2 - K.g2 * cs2)};
+        const Real Rs[4] = {-af * cf, csl * as * b1 * sg, csl * as * b2 * sg, -Gf};
+        pair(0, Lc, Ls, Rc, Rs);
+    }
+    {
+        const Real k2 = -K.gm1 * as;
+        const Real Lc[7] = {pre * K.g1 * as * v2, pre * k2 * vn, pre * k2 * vt1, pre * k2 * vt2,
+                            pre * (k2 * Bt1 - sr * cs * af * b1), pre * (k2 * Bt2 - sr * cs * af * b2), pre * K.gm1 * as};
+        const Real Ls[4] = {pre * Gs, -pre * as * csl, -pre * cf * af * b1 * sg, -pre * cf * af * b2 * sg};
+        const Real Rc[7] = {as, as * vn, as * vt1, as * vt2, -cs * af * b1 * isr, -cs * af * b2 * isr,
+                            as * (Real(0.5) * v2 + csl2 - K.g2 * cs2)};
+        const Real Rs[4] = {-as * csl, -cf * af * b1 * sg, -cf * af * b2 * sg, -Gs};
+        pair(2, Lc, Ls, Rc, Rs);
+    }
+    {
+        const Real l0 = Real(0.5) * Ga, l2 = Real(-0.5) * b2 * sg, l3 = Real(0.5) * b1 * sg;
+        const Real l4 = Real(-0.5) * sr * b2, l5 = Real(0.5) * sr * b1;
+        const Real z = Real(0);
+        const Real La[7] = {l0, z, l2, l3, l4, l5, z}, Lb[7] = {l0, z, l2, l3, -l4, -l5, z};
+        const Real Ra[7] = {z, z, -b2 * sg, b1 * sg, -b2 * isr, b1 * isr, -Ga};
+        const Real Rb[7] = {z, z, -b2 * sg, b1 * sg, b2 * isr, -b1 * isr, -Ga};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            L[4][c] = La[c];
+            L[5][c] = Lb[c];
+            R[4][c] = Ra[c];
+            R[5][c] = Rb[c];
+        }
+    }
+    {
+        const Real Le[7] = {Real(1) - Real(0.5) * tau * v2, tau * vn, tau * vt1, tau * vt2, tau * Bt1, tau * Bt2, -tau};
+        const Real Re[7] = {Real(1), vn, vt1, vt2, Real(0), Real(0), Real(0.5) * v2};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            L[6][c] = Le[c];
+            R[6][c] = Re[c];
+        }
+    }
+}
+
+// weno_field (Eq. FWENO for one characteristic field) and its gradient in
+// its eleven projections and in alpha: the two phi_N evaluations run on dual
+// numbers seeded in their four arguments.
+template <typename B, int VAR>
+__device__ __forceinline__ void weno_field_grad(const B (&P)[11], B alpha, B eps4, B &phi, B (&gP)[11], B &galpha) {
+    using D4 = Dual<B, 4>;
+    B p[5], q[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        p[j] = P[1 + j] + alpha * P[6 + j];
+        q[j] = P[1 + j] - alpha * P[6 + j];
+    }
+    D4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        a[i] = D4((double)p[i]);
+        a[i].d[i] = B(1);
+        b[i] = D4((double)q[4 - i]);
+        b[i].d[i] = B(1);
+    }
+    const D4 e4((double)eps4);
+    const D4 fp = phi_n<D4, VAR>(a[0], a[1], a[2], a[3], e4);
+    const D4 fq = phi_n<D4, VAR>(b[0], b[1], b[2], b[3], e4);
+    phi = P[0] + B(0.5) * (fq.v - fp.v);
+    B gp[5], gq[5];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gp[j] = B(-0.5) * fp.d[j];
+    gp[4] = B(0);
+    gq[0] = B(0);
+#pragma unroll
+    for (int j = 1; j < 5; ++j) gq[j] = B(0.5) * fq.d[4 - j];
+    gP[0] = B(1);
+    galpha = B(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        gP[1 + j] = gp[j] + gq[j];
+        gP[6 + j] = alpha * (gp[j] - gq[j]);
+        galpha = galpha + P[6 + j] * (gp[j] - gq[j]);
+    }
+}
+
+// Reverse mode of the face function.  Face p (the interface between cell p
+// and its successor along AX) reads stencil cells p-2 .. p+3 (inputs rho,
+// m_x, m_y, m_z, E, B_x, B_y, B_z each); its outputs are the five lab-order
+// face fluxes and the two transport fluxes.  One primal evaluation (the
+// formulas of cell_fill and face_flux), then the transposes of the linear
+// parts (stencil combinations, projection on the left eigenvectors,
+// back-projection on the right ones), with dual numbers only where the
+// dependence is nonlinear and narrow: the eigenvectors on the eight
+// interface values, each phi_N on its four arguments, each cell's 23
+// quantities on its eight inputs.  Branches follow the primal values (the
+// derivative of the branch the forward step takes).  The 48 contributions
+// d(lam . outputs)/d(input) go to cb; adjoints accumulate in double (float
+// in the float path, whose Jacobians are float).
 template <int AX, typename B, int VAR>
-__global__ void __launch_bounds__(128) adj_sweep_kernel(AdjSweepArgs<B> a) {
-    constexpr int ND = kAdjND;
-    using D = Dual<B, ND>;
+__global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
+    using D8 = Dual<B, 8>;
+    using A = typename std::conditional<std::is_same<B, float>::value, float, double>::type;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = (long long)nx * ny * nz;
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -66,44 +229,172 @@ __global__ void __launch_bounds__(128) adj_sweep_kernel(AdjSweepArgs<B> a) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) in[s][5 + f] = a.bc[f][g];
     }
-    // adjoints of the outputs in the frame order of face_flux
-    double lam[7];
-    lam[0] = a.lamF[0][p];
-    lam[1] = a.lamF[1 + AX][p];
-    lam[2] = a.lamF[1 + (AX + 1) % 3][p];
-    lam[3] = a.lamF[1 + (AX + 2) % 3][p];
-    lam[4] = a.lamF[4][p];
-    lam[5] = a.lamS[0][p];
-    lam[6] = a.lamS[1][p];
-    const Phys<D> K = promote<B, ND>(a.K);
+    const A lam5 = (A)a.lamS[0][p], lam6 = (A)a.lamS[1][p];
+    // adjoint of the frame flux Ff (s1 = Ff[4] + bvt1, s2 = Ff[5] + bvt2)
+    A lFf[7];
+    lFf[0] = (A)a.lamF[0][p];
+    lFf[1] = (A)a.lamF[1 + AX][p];
+    lFf[2] = (A)a.lamF[1 + (AX + 1) % 3][p];
+    lFf[3] = (A)a.lamF[1 + (AX + 2) % 3][p];
+    lFf[4] = (A)lam5;
+    lFf[5] = (A)lam6;
+    lFf[6] = (A)a.lamF[4][p];
+    const Phys<B> K = a.K;
     bool bad = false, hit = false;
-    // the six cells' quantities without tangents; a pass seeds one cell
-    D cq[NCQ * 6];
-    auto fill = [&](int c, int seed0) {
-        D x[8];
+    B cq[NCQ * 6];
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c)
+        cell_fill<B, AX>(cq + c, 6, in[c][0], in[c][1], in[c][2], in[c][3], in[c][4], in[c][5], in[c][6], in[c][7], K,
+                         bad, hit);
+#define Q(q, kk) cq[(q) * 6 + (kk)]
+    constexpr int qU[7] = {C_RHOQ, C_MN, C_MT1, C_MT2, C_BT1, C_BT2, C_E};
+    B X[11][7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        const B f0 = Q(C_F0 + c, 0), f1 = Q(C_F0 + c, 1), f2 = Q(C_F0 + c, 2), f3 = Q(C_F0 + c, 3), f4 = Q(C_F0 + c, 4),
+                f5 = Q(C_F0 + c, 5);
+        X[0][c] = (B(7) * (f2 + f3) - (f1 + f4)) * B(1.0 / 12.0);
+        X[1][c] = f1 - f0;
+        X[2][c] = f2 - f1;
+        X[3][c] = f3 - f2;
+        X[4][c] = f4 - f3;
+        X[5][c] = f5 - f4;
+        const B u0 = Q(qU[c], 0), u1 = Q(qU[c], 1), u2 = Q(qU[c], 2), u3 = Q(qU[c], 3), u4 = Q(qU[c], 4),
+                u5 = Q(qU[c], 5);
+        X[6][c] = u1 - u0;
+        X[7][c] = u2 - u1;
+        X[8][c] = u3 - u2;
+        X[9][c] = u4 - u3;
+        X[10][c] = u5 - u4;
+    }
+    // LF speeds alpha(m) = max over cells 2, 3 of |v_n + sgn c|, with the
+    // cell and sign that attain it (the branch the forward step takes)
+    constexpr int cq_of_mode[7] = {C_CF, C_CF, C_CSL, C_CSL, C_CA, C_CA, -1};
+    constexpr int sgn_of_mode[7] = {-1, 1, -1, 1, -1, 1, 0};
+    B alpha[7];
+    int acell[7];
+    B asign[7];
+#pragma unroll
+    for (int mo = 0; mo < 7; ++mo) {
+        const B c2 = cq_of_mode[mo] >= 0 ? Q(cq_of_mode[mo], 2) : B(0);
+        const B c3 = cq_of_mode[mo] >= 0 ? Q(cq_of_mode[mo], 3) : B(0);
+        const B x2 = Q(C_VN, 2) + B(sgn_of_mode[mo]) * c2, x3 = Q(C_VN, 3) + B(sgn_of_mode[mo]) * c3;
+        const B a2 = x2 >= B(0) ? x2 : -x2, a3 = x3 >= B(0) ? x3 : -x3;
+        acell[mo] = a2 >= a3 ? 2 : 3;
+        alpha[mo] = a2 >= a3 ? a2 : a3;
+        asign[mo] = (a2 >= a3 ? x2 : x3) >= B(0) ? B(1) : B(-1);
+    }
+    // eigenvectors on dual numbers over the interface state
+    D8 wd[8];
+    const int prim[8] = {C_RHO, C_VN, C_VT1, C_VT2, C_BN, C_BT1, C_BT2, C_P};
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        wd[t] = D8((double)(B(0.5) * (Q(prim[t], 2) + Q(prim[t], 3))));
+        wd[t].d[t] = B(1);
+    }
+    D8 Ld[7][7], Rd[7][7];
+    eigen7<D8>(wd, promote<B, 8>(K), Ld, Rd);
+    const B eps4 = B(4) * K.eps_w;
+    A lX[11][7];
+#pragma unroll
+    for (int x = 0; x < 11; ++x)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) lX[x][c] = A(0);
+    A lw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    A lalpha[7];
+#pragma unroll 1
+    for (int mo = 0; mo < 7; ++mo) {
+        B Pm[11];
+#pragma unroll
+        for (int x = 0; x < 11; ++x) {
+            B acc = Ld[mo][0].v * X[x][0];
+#pragma unroll
+            for (int c = 1; c < 7; ++c) acc = acc + Ld[mo][c].v * X[x][c];
+            Pm[x] = acc;
+        }
+        B phi, gP[11], ga;
+        weno_field_grad<B, VAR>(Pm, alpha[mo], eps4, phi, gP, ga);
+        A lphi = A(0);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) lphi += (A)Rd[mo][c].v * lFf[c];
+        lalpha[mo] = lphi * (A)ga;
+        A lL[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int x = 0; x < 11; ++x) {
+            const A lp = lphi * (A)gP[x];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                lX[x][c] += lp * (A)Ld[mo][c].v;
+                lL[c] += lp * (A)X[x][c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const A lR = (A)phi * lFf[c];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) lw[t] += lL[c] * (A)Ld[mo][c].d[t] + lR * (A)Rd[mo][c].d[t];
+        }
+    }
+    // adjoints of the cells' quantities
+    A lq[6][NCQ];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int q = 0; q < NCQ; ++q) lq[c][q] = A(0);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        // X[0] = (7 (f2 + f3) - (f1 + f4)) / 12, X[1 + k] = f_{k+1} - f_k, X[6 + k] = u_{k+1} - u_k
+        const A l0 = lX[0][c] * A(1.0 / 12.0);
+        lq[1][C_F0 + c] -= l0;
+        lq[2][C_F0 + c] += A(7) * l0;
+        lq[3][C_F0 + c] += A(7) * l0;
+        lq[4][C_F0 + c] -= l0;
+#pragma unroll
+        for (int kk = 0; kk < 5; ++kk) {
+            lq[kk + 1][C_F0 + c] += lX[1 + kk][c];
+            lq[kk][C_F0 + c] -= lX[1 + kk][c];
+            lq[kk + 1][qU[c]] += lX[6 + kk][c];
+            lq[kk][qU[c]] -= lX[6 + kk][c];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        lq[2][prim[t]] += A(0.5) * lw[t];
+        lq[3][prim[t]] += A(0.5) * lw[t];
+    }
+#pragma unroll
+    for (int mo = 0; mo < 7; ++mo) {
+        const A g = lalpha[mo] * (A)asign[mo];
+        lq[acell[mo]][C_VN] += g;
+        if (cq_of_mode[mo] >= 0) lq[acell[mo]][cq_of_mode[mo]] += g * A(sgn_of_mode[mo]);
+    }
+    // transport fluxes bvt = (B_n v_t (cell 2) + B_n v_t (cell 3)) / 2
+#pragma unroll
+    for (int c = 2; c <= 3; ++c) {
+        lq[c][C_BN] += A(0.5) * (lam5 * (A)Q(C_VT1, c) + lam6 * (A)Q(C_VT2, c));
+        lq[c][C_VT1] += A(0.5) * lam5 * (A)Q(C_BN, c);
+        lq[c][C_VT2] += A(0.5) * lam6 * (A)Q(C_BN, c);
+    }
+#undef Q
+    // each cell's quantities on its eight inputs
+    const Phys<D8> KD = promote<B, 8>(K);
+#pragma unroll 1
+    for (int c = 0; c < 6; ++c) {
+        D8 x[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            x[v] = D((double)in[c][v]);
-            if (v >= seed0 && v < seed0 + ND) x[v].d[v - seed0] = B(1);
+            x[v] = D8((double)in[c][v]);
+            x[v].d[v] = B(1);
         }
-        cell_fill<D, AX>(cq + c, 6, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], K, bad, hit);
-    };
-#pragma unroll 1
-    for (int c = 0; c < 6; ++c) fill(c, -ND);
-#pragma unroll 1
-    for (int pass = 0; pass < 6 * (8 / ND); ++pass) {
-        const int s = pass / (8 / ND), v0 = (pass % (8 / ND)) * ND;
-        fill(s, v0);
-        D Ff[7], s1, s2;
-        face_flux<D, VAR>(cq, 6, 1, K, Ff, s1, s2);
+        D8 qd[NCQ];
+        cell_fill<D8, AX>(qd, 1, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], KD, bad, hit);
 #pragma unroll
-        for (int t = 0; t < ND; ++t) {
-            const double g = lam[0] * (double)Ff[0].d[t] + lam[1] * (double)Ff[1].d[t] + lam[2] * (double)Ff[2].d[t] +
-                             lam[3] * (double)Ff[3].d[t] + lam[4] * (double)Ff[6].d[t] + lam[5] * (double)s1.d[t] +
-                             lam[6] * (double)s2.d[t];
-            a.cb[(size_t)(s * 8 + v0 + t) * (size_t)n + (size_t)p] = g;
+        for (int v = 0; v < 8; ++v) {
+            A g = A(0);
+#pragma unroll
+            for (int q = 0; q < NCQ; ++q) g += lq[c][q] * (A)qd[q].d[v];
+            a.cb[(size_t)(c * 8 + v) * (size_t)n + (size_t)p] = (double)g;
         }
-        fill(s, -ND);       // back to no tangents
     }
 }
 
@@ -414,11 +705,11 @@ cudaError_t launch_adj_sweep_impl(int axis, const AdjSweepArgs<B> &a, cudaStream
     const long long n = (long long)a.nx * a.ny * a.nz;
     const unsigned nb = (unsigned)((n + 127) / 128);
     if (axis == 0)
-        adj_sweep_kernel<0, B, VAR><<<nb, 128, 0, s>>>(a);
+        adj_face_kernel<0, B, VAR><<<nb, 128, 0, s>>>(a);
     else if (axis == 1)
-        adj_sweep_kernel<1, B, VAR><<<nb, 128, 0, s>>>(a);
+        adj_face_kernel<1, B, VAR><<<nb, 128, 0, s>>>(a);
     else
-        adj_sweep_kernel<2, B, VAR><<<nb, 128, 0, s>>>(a);
+        adj_face_kernel<2, B, VAR><<<nb, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
