@@ -337,6 +337,15 @@ def run_native(args):
                    max(np.abs(c64h).max(), np.abs(b64h).max()))
     del c64, b64, c32, b32
 
+    # ---- WENO-JS, both forms, same steps (the robust variant)
+    sjs, msjs, _, _, _, _ = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP64, args.steps, args.warmup,
+                                      None, None, barrier, variant=w5.W5CT_WENO_JS)
+    sjs.close()
+    fjs, msfjs, _, _, _, _ = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP32_BULK, args.steps,
+                                       args.warmup, None, None, barrier, variant=w5.W5CT_WENO_JS)
+    fjs.close()
+    msjs, msfjs = max_over_ranks(msjs), max_over_ranks(msfjs)
+
     # ---- end to end through the C ABI with host buffers (FP64)
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     hc = torch.from_numpy(cons).pin_memory()
@@ -402,6 +411,10 @@ def run_native(args):
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "gpu_launches": launches32,
         },
+        "weno_js": {"fp64_value": replica_throughput(world, zones, args.steps, msjs),
+                    "fp64_ms_per_step": msjs / args.steps,
+                    "fp32_bulk_value": replica_throughput(world, zones, args.steps, msfjs),
+                    "fp32_bulk_ms_per_step": msfjs / args.steps},
         "div_b_linf": divb64,
         "e2e": {"value": world * zones * e2e_steps / e2e_s, "unit": "zone-updates/s",
                 "h2d_bytes_per_step": int(cons.nbytes + bface.nbytes),
@@ -416,6 +429,25 @@ def run_native(args):
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (or its architecture when /proc does not say)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        import platform
+        parts = {}
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                parts.setdefault(k.strip(), v.strip())
+        return f"{platform.machine()} implementer {parts.get('CPU implementer', '?')} part {parts.get('CPU part', '?')}"
+    except OSError:
+        import platform
+        return platform.machine()
 
 
 def cpu_baseline(args):
@@ -437,9 +469,24 @@ def cpu_baseline(args):
         el = time.perf_counter() - t0
         if el >= args.cpu_seconds:
             break
-    return {"value": ns ** 3 * steps / el, "unit": "zone-updates/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{steps} full steps of a {ns}^3 box of the same turbulence generator",
-            "seconds": el}
+    cores = oracle.num_threads()
+    value = ns ** 3 * steps / el
+    # the same sample on one core, for about a quarter of the time
+    oracle.set_num_threads(1)
+    o.set_state(cons, bface)
+    steps1 = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(o.cfl_dt())
+        steps1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= 0.25 * args.cpu_seconds:
+            break
+    oracle.set_num_threads(cores)
+    return {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full steps of a {ns}^3 box of the same turbulence generator",
+            "seconds": el, "single_core_value": ns ** 3 * steps1 / el1, "single_core_steps": steps1,
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_blast(args):

@@ -82,6 +82,8 @@ def _load():
         lib.ora_weno_char_flux.argtypes = [_DP, _DP, c_double, POINTER(OracleConfig)]
         lib.ora_weno_char_flux.restype = c_double
         lib.ora_num_threads.restype = c_int
+        lib.ora_set_num_threads.argtypes = [c_int]
+        lib.ora_set_num_threads.restype = c_int
         _lib = lib
     return _lib
 
@@ -102,6 +104,11 @@ def _check(rc: int, what: str):
 
 def num_threads() -> int:
     return int(_load().ora_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Host threads of the oracle's following calls."""
+    _check(_load().ora_set_num_threads(int(n)), "set_num_threads")
 
 
 class Oracle:

@@ -106,6 +106,16 @@ int ora_num_threads(void) {
 #endif
 }
 
+/* Host threads of the following calls (n >= 1); used to time the oracle on
+ * one core and on all cores. */
+int ora_set_num_threads(int n) {
+    if (n < 1) return -1;
+#ifdef _OPENMP
+    omp_set_num_threads(n);
+#endif
+    return 0;
+}
+
 int ora_create(const ora_config *cfg, ora_ctx **out) {
     if (!cfg || !out) return ORA_ERR_ARG;
     if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return ORA_ERR_ARG;
