@@ -50,6 +50,8 @@ extern "C" {
 #define W5CT_ERR_STATE (-3)        /* call out of order (e.g. step before set_state) */
 #define W5CT_ERR_NONPHYSICAL (-4)  /* rho <= 0, P <= 0 or NaN met inside the scheme */
 #define W5CT_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
+#define W5CT_ERR_TIMEOUT (-6)      /* a bounded device wait expired; reserved: no kernel of
+                                      this build waits on another block or on the host */
 
 #define W5CT_WENO_JS 0             /* Jiang-Shu weights, eps = 1e-6 (Sec. 2.2) */
 #define W5CT_WENO_Z 1              /* WENO-Z weights (Sec. 2.2), ratio squared */

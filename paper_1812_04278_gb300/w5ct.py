@@ -30,6 +30,7 @@ W5CT_ERR_CUDA = -2
 W5CT_ERR_STATE = -3
 W5CT_ERR_NONPHYSICAL = -4
 W5CT_ERR_UNSUPPORTED = -5
+W5CT_ERR_TIMEOUT = -6
 W5CT_WENO_JS = 0
 W5CT_WENO_Z = 1
 W5CT_FP64 = 0
