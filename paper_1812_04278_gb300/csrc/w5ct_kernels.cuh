@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kCellBlock) speed_batched_kernel(const PatchGe
         cell_speeds<Real>(q0[p], q1[p], q2[p], q3[p], q4[p], B0[p], B1[p], B2[p], K, v, bad);
     }
     if (bad) atomicOr(flag, 1);
-    // block maxima over the 8 warps of the 32 x 8 block
+    // block maxima over the 8 warps of the 256-thread block
     __shared__ double red2[3 * 32];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
