@@ -20,8 +20,10 @@ cudaError_t launch_sweep(int axis, int variant, const SweepArgs<Real> &a, cudaSt
 template <typename Real>
 struct SweepTuning;
 
-// Defaults measured on GB300 at 256^3 (FP32: 2 blocks/SM of 16-high tiles,
-// 1.6x faster than 1 block of 8-high tiles).
+// Defaults measured on GB300 (FP32 at 256^3: 2 blocks/SM of 16-high tiles,
+// 1.6x faster than 1 block of 8-high tiles; 3 blocks/SM or 32-high y/z tiles
+// are slower.  FP64 at 128^3: FP64-pipe bound, within 1% for 8- or 16-high
+// tiles and 1 or 2 blocks/SM; 16-high on every axis is the fastest).
 #ifndef W5CT_F32_T2X
 #define W5CT_F32_T2X 16
 #endif
@@ -32,10 +34,13 @@ struct SweepTuning;
 #define W5CT_F32_MINB 2
 #endif
 #ifndef W5CT_F64_T2X
-#define W5CT_F64_T2X 8
+#define W5CT_F64_T2X 16
 #endif
 #ifndef W5CT_F64_T2YZ
 #define W5CT_F64_T2YZ 16
+#endif
+#ifndef W5CT_F64_MINB
+#define W5CT_F64_MINB 1
 #endif
 
 template <>
@@ -44,7 +49,7 @@ struct SweepTuning<float> {
 };
 template <>
 struct SweepTuning<double> {
-    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = 1;
+    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = W5CT_F64_MINB;
 };
 
 template <int AX, typename Real>
