@@ -193,16 +193,140 @@ __device__ __forceinline__ void weno_field_grad(const B (&P)[11], B alpha, B eps
     }
 }
 
+// Reverse of cell_fill<B, AX>: given the adjoints lq of a cell's 23
+// quantities, the adjoints of its eight inputs (rho, m_x, m_y, m_z, E, B_x,
+// B_y, B_z) in out.  The primitives and the flux are differentiated by hand
+// (Eq. P and Eq. fluxes); the three wave speeds, when their adjoints are not
+// zero (the two cells next to the face), on dual numbers over (rho, P, B_n,
+// B_t1, B_t2).  The floors, when they apply, cut the dependence as in the
+// forward step.
+template <typename B, typename A, int AX>
+__device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq)[NCQ], const Phys<B> &K,
+                                                  A (&out)[8]) {
+    constexpr int n = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
+    const B rho = in[0], mn = in[1 + n], m1 = in[1 + t1], m2 = in[1 + t2], E = in[4];
+    const B Bn = in[5 + n], B1 = in[5 + t1], B2 = in[5 + t2];
+    B r = rho;
+    bool rfloor = false, pfloor = false;
+    if (K.floors && r < K.rho_min) {
+        r = K.rho_min;
+        rfloor = true;
+    }
+    const B ir = M<B>::rcp_(r);
+    const A vn = (A)(mn * ir), v1 = (A)(m1 * ir), v2 = (A)(m2 * ir);
+    const A vv = vn * vn + v1 * v1 + v2 * v2;
+    const A BB = (A)Bn * (A)Bn + (A)B1 * (A)B1 + (A)B2 * (A)B2;
+    B P = K.gm1 * (E - B(0.5) * r * (B)vv - B(0.5) * (B)BB);
+    if (K.floors && P < K.p_min) {
+        P = K.p_min;
+        pfloor = true;
+    }
+    const A rA = (A)r, PA = (A)P, EA = (A)E, bn = (A)Bn, b1 = (A)B1, b2 = (A)B2;
+    const A Pt = PA + A(0.5) * BB;
+    const A vB = vn * bn + v1 * b1 + v2 * b2;
+    A lr = lq[C_RHO], lvn = lq[C_VN], lv1 = lq[C_VT1], lv2 = lq[C_VT2];
+    A lBn = lq[C_BN], lB1 = lq[C_BT1], lB2 = lq[C_BT2], lP = lq[C_P];
+    A lE = lq[C_E], lmn = lq[C_MN], lm1 = lq[C_MT1], lm2 = lq[C_MT2], lrho = lq[C_RHOQ];
+    A lPt = A(0), lvB = A(0);
+    {   // F0 = r vn, F1 = r vn^2 + Pt - Bn^2, F2 = r vn v1 - Bn B1, F3 = r vn v2 - Bn B2
+        const A f0 = lq[C_F0], f1 = lq[C_F1], f2 = lq[C_F2], f3 = lq[C_F3];
+        lr += f0 * vn + f1 * vn * vn + f2 * vn * v1 + f3 * vn * v2;
+        lvn += f0 * rA + f1 * A(2) * rA * vn + f2 * rA * v1 + f3 * rA * v2;
+        lPt += f1;
+        lBn -= f1 * A(2) * bn + f2 * b1 + f3 * b2;
+        lv1 += f2 * rA * vn;
+        lv2 += f3 * rA * vn;
+        lB1 -= f2 * bn;
+        lB2 -= f3 * bn;
+    }
+    {   // F4 = B1 vn - Bn v1, F5 = B2 vn - Bn v2, F6 = (E + Pt) vn - Bn vB
+        const A f4 = lq[C_F4], f5 = lq[C_F5], f6 = lq[C_F6];
+        lB1 += f4 * vn;
+        lB2 += f5 * vn;
+        lvn += f4 * b1 + f5 * b2 + f6 * (EA + Pt);
+        lBn -= f4 * v1 + f5 * v2 + f6 * vB;
+        lv1 -= f4 * bn;
+        lv2 -= f5 * bn;
+        lE += f6 * vn;
+        lPt += f6 * vn;
+        lvB -= f6 * bn;
+    }
+    // vB = vn Bn + v1 B1 + v2 B2; Pt = P + BB/2
+    lvn += lvB * bn;
+    lv1 += lvB * b1;
+    lv2 += lvB * b2;
+    lBn += lvB * vn + lPt * bn;
+    lB1 += lvB * v1 + lPt * b1;
+    lB2 += lvB * v2 + lPt * b2;
+    lP += lPt;
+    // wave speeds on dual numbers over (r, P, Bn, B1, B2)
+    const A lcf = lq[C_CF], lca = lq[C_CA], lcs = lq[C_CSL];
+    if (lcf != A(0) || lca != A(0) || lcs != A(0)) {
+        using D5 = Dual<B, 5>;
+        using m5 = M<D5>;
+        D5 x[5];
+        const B xv[5] = {r, P, Bn, B1, B2};
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            x[t] = D5((double)xv[t]);
+            x[t].d[t] = B(1);
+        }
+        const D5 irr = m5::rcp_(x[0]);
+        const D5 cs2 = D5((double)K.gamma) * x[1] * irr;
+        const D5 ca2 = x[2] * x[2] * irr;
+        const D5 bt2 = (x[3] * x[3] + x[4] * x[4]) * irr;
+        D5 fmc, cms, cf2, csl2;
+        speeds<D5>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+        const D5 cf = m5::sqrt_(cf2), csl = m5::sqrt_(csl2);
+        const D5 ca = m5::abs_(x[2]) * (m5::sqrt_(x[0]) * irr);
+        A g[5];
+#pragma unroll
+        for (int t = 0; t < 5; ++t) g[t] = lcf * (A)cf.d[t] + lca * (A)ca.d[t] + lcs * (A)csl.d[t];
+        lr += g[0];
+        lP += g[1];
+        lBn += g[2];
+        lB1 += g[3];
+        lB2 += g[4];
+    }
+    // P = gm1 (E - r vv / 2 - BB / 2)
+    if (!pfloor) {
+        const A gl = (A)K.gm1 * lP;
+        lE += gl;
+        lr -= A(0.5) * vv * gl;
+        lvn -= rA * vn * gl;
+        lv1 -= rA * v1 * gl;
+        lv2 -= rA * v2 * gl;
+        lBn -= bn * gl;
+        lB1 -= b1 * gl;
+        lB2 -= b2 * gl;
+    }
+    // v = m / r
+    const A irA = (A)ir;
+    lmn += lvn * irA;
+    lm1 += lv1 * irA;
+    lm2 += lv2 * irA;
+    lr -= (lvn * vn + lv1 * v1 + lv2 * v2) * irA;
+    if (!rfloor) lrho += lr;
+    out[0] = lrho;
+    out[1 + n] = lmn;
+    out[1 + t1] = lm1;
+    out[1 + t2] = lm2;
+    out[4] = lE;
+    out[5 + n] = lBn;
+    out[5 + t1] = lB1;
+    out[5 + t2] = lB2;
+}
+
 // Reverse mode of the face function.  Face p (the interface between cell p
 // and its successor along AX) reads stencil cells p-2 .. p+3 (inputs rho,
 // m_x, m_y, m_z, E, B_x, B_y, B_z each); its outputs are the five lab-order
 // face fluxes and the two transport fluxes.  One primal evaluation (the
 // formulas of cell_fill and face_flux), then the transposes of the linear
 // parts (stencil combinations, projection on the left eigenvectors,
-// back-projection on the right ones), with dual numbers only where the
-// dependence is nonlinear and narrow: the eigenvectors on the eight
-// interface values, each phi_N on its four arguments, each cell's 23
-// quantities on its eight inputs.  Branches follow the primal values (the
+// back-projection on the right ones) and of the cell recovery
+// (cell_fill_adjoint), with dual numbers only where the dependence is
+// nonlinear and narrow: the eigenvectors on the eight interface values, each
+// phi_N on its four arguments, the wave speeds of the two central cells.  Branches follow the primal values (the
 // derivative of the branch the forward step takes).  The 48 contributions
 // d(lam . outputs)/d(input) go to cb; adjoints accumulate in double (float
 // in the float path, whose Jacobians are float).
@@ -376,25 +500,13 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
         lq[c][C_VT2] += A(0.5) * lam6 * (A)Q(C_BN, c);
     }
 #undef Q
-    // each cell's quantities on its eight inputs
-    const Phys<D8> KD = promote<B, 8>(K);
+    // each cell's quantities back to its eight inputs
 #pragma unroll 1
     for (int c = 0; c < 6; ++c) {
-        D8 x[8];
+        A g[8];
+        cell_fill_adjoint<B, A, AX>(in[c], lq[c], K, g);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            x[v] = D8((double)in[c][v]);
-            x[v].d[v] = B(1);
-        }
-        D8 qd[NCQ];
-        cell_fill<D8, AX>(qd, 1, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], KD, bad, hit);
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            A g = A(0);
-#pragma unroll
-            for (int q = 0; q < NCQ; ++q) g += lq[c][q] * (A)qd[q].d[v];
-            a.cb[(size_t)(c * 8 + v) * (size_t)n + (size_t)p] = (double)g;
-        }
+        for (int v = 0; v < 8; ++v) a.cb[(size_t)(c * 8 + v) * (size_t)n + (size_t)p] = (double)g[v];
     }
 }
 
