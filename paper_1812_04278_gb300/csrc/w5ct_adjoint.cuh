@@ -152,37 +152,90 @@ __device__ __forceinline__ void eigen7(const Real (&w)[8], const Phys<Real> &K, 
     }
 }
 
+// phi_N(a, b, c, d) of Sec. 2.2 (the weights of the forward step: JS, or
+// WENO-Z with the ratio clamped at 1e18 in float) and its gradient in (a, b,
+// c, d), by hand: smoothness indicators -> weights (through tau for WENO-Z)
+// -> the two interpolants, run backwards.
+template <typename B, int VAR>
+__device__ __forceinline__ void phi_n_grad(B a, B b, B c, B d, B eps, B &phi, B (&g)[4]) {
+    const B x0 = a - b, x1 = a - B(3) * b, y0 = b - c, y1 = b + c, z0 = c - d, z1 = B(3) * c - d;
+    const B IS0 = B(13) * x0 * x0 + B(3) * x1 * x1;
+    const B IS1 = B(13) * y0 * y0 + B(3) * y1 * y1;
+    const B IS2 = B(13) * z0 * z0 + B(3) * z1 * z1;
+    const B s[3] = {eps + IS0, eps + IS1, eps + IS2};
+    const B dk[3] = {B(1), B(6), B(3)};
+    B al[3], r[3], t = B(0);
+    bool clamped[3] = {false, false, false};
+    if constexpr (VAR == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) al[k] = dk[k] / (s[k] * s[k]);
+    } else {
+        t = IS0 - IS2;
+        const B tau = t >= B(0) ? t : -t;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            r[k] = tau / s[k];
+            if constexpr (float_based<B>) {
+                if (r[k] > B(1.0e18)) {
+                    r[k] = B(1.0e18);
+                    clamped[k] = true;
+                }
+            }
+            al[k] = dk[k] * (B(1) + r[k] * r[k]);
+        }
+    }
+    const B S = al[0] + al[1] + al[2];
+    const B w0 = al[0] / S, w2 = al[2] / S;
+    const B t1 = a - B(2) * b + c, t2 = b - B(2) * c + d;
+    phi = w0 * B(1.0 / 3.0) * t1 + (w2 - B(0.5)) * B(1.0 / 6.0) * t2;
+    // backwards, with d(phi) = 1
+    const B lw0 = t1 * B(1.0 / 3.0), lw2 = t2 * B(1.0 / 6.0);
+    const B lt1 = w0 * B(1.0 / 3.0), lt2 = (w2 - B(0.5)) * B(1.0 / 6.0);
+    const B common = (lw0 * w0 + lw2 * w2) / S;
+    const B la[3] = {lw0 / S - common, -common, lw2 / S - common};
+    B lIS[3];
+    if constexpr (VAR == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lIS[k] = la[k] * (B(-2) * al[k] / s[k]);
+    } else {
+        B ltau = B(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const B lr = clamped[k] ? B(0) : la[k] * dk[k] * B(2) * r[k];
+            ltau = ltau + lr / s[k];
+            lIS[k] = -lr * r[k] / s[k];
+        }
+        const B lt = t >= B(0) ? ltau : -ltau;
+        lIS[0] = lIS[0] + lt;
+        lIS[2] = lIS[2] - lt;
+    }
+    g[0] = lIS[0] * (B(26) * x0 + B(6) * x1) + lt1;
+    g[1] = lIS[0] * (B(-26) * x0 - B(18) * x1) + lIS[1] * (B(26) * y0 + B(6) * y1) - B(2) * lt1 + lt2;
+    g[2] = lIS[1] * (B(-26) * y0 + B(6) * y1) + lIS[2] * (B(26) * z0 + B(18) * z1) + lt1 - B(2) * lt2;
+    g[3] = lIS[2] * (B(-26) * z0 - B(6) * z1) + lt2;
+}
+
 // weno_field (Eq. FWENO for one characteristic field) and its gradient in
-// its eleven projections and in alpha: the two phi_N evaluations run on dual
-// numbers seeded in their four arguments.
+// its eleven projections and in alpha.
 template <typename B, int VAR>
 __device__ __forceinline__ void weno_field_grad(const B (&P)[11], B alpha, B eps4, B &phi, B (&gP)[11], B &galpha) {
-    using D4 = Dual<B, 4>;
     B p[5], q[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         p[j] = P[1 + j] + alpha * P[6 + j];
         q[j] = P[1 + j] - alpha * P[6 + j];
     }
-    D4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        a[i] = D4((double)p[i]);
-        a[i].d[i] = B(1);
-        b[i] = D4((double)q[4 - i]);
-        b[i].d[i] = B(1);
-    }
-    const D4 e4((double)eps4);
-    const D4 fp = phi_n<D4, VAR>(a[0], a[1], a[2], a[3], e4);
-    const D4 fq = phi_n<D4, VAR>(b[0], b[1], b[2], b[3], e4);
-    phi = P[0] + B(0.5) * (fq.v - fp.v);
+    B fp, fq, gpa[4], gqa[4];
+    phi_n_grad<B, VAR>(p[0], p[1], p[2], p[3], eps4, fp, gpa);
+    phi_n_grad<B, VAR>(q[4], q[3], q[2], q[1], eps4, fq, gqa);
+    phi = P[0] + B(0.5) * (fq - fp);
     B gp[5], gq[5];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) gp[j] = B(-0.5) * fp.d[j];
+    for (int j = 0; j < 4; ++j) gp[j] = B(-0.5) * gpa[j];
     gp[4] = B(0);
     gq[0] = B(0);
 #pragma unroll
-    for (int j = 1; j < 5; ++j) gq[j] = B(0.5) * fq.d[4 - j];
+    for (int j = 1; j < 5; ++j) gq[j] = B(0.5) * gqa[4 - j];
     gP[0] = B(1);
     galpha = B(0);
 #pragma unroll
@@ -323,11 +376,12 @@ __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq
 // face fluxes and the two transport fluxes.  One primal evaluation (the
 // formulas of cell_fill and face_flux), then the transposes of the linear
 // parts (stencil combinations, projection on the left eigenvectors,
-// back-projection on the right ones) and of the cell recovery
-// (cell_fill_adjoint), with dual numbers only where the dependence is
-// nonlinear and narrow: the eigenvectors on the eight interface values, each
-// phi_N on its four arguments, the wave speeds of the two central cells.  Branches follow the primal values (the
-// derivative of the branch the forward step takes).  The 48 contributions
+// back-projection on the right ones), of phi_N (phi_n_grad) and of the cell
+// recovery (cell_fill_adjoint), with dual numbers only where the dependence
+// is nonlinear and narrow: the eigenvectors on the eight interface values
+// and the wave speeds of the two central cells.  Branches follow the primal
+// values (the derivative of the branch the forward step takes).  The 48
+// contributions
 // d(lam . outputs)/d(input) go to cb; adjoints accumulate in double (float
 // in the float path, whose Jacobians are float).
 template <int AX, typename B, int VAR>
