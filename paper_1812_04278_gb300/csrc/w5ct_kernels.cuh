@@ -160,14 +160,17 @@ __device__ __forceinline__ void cellb_cell(int nx, int ny, int nz, size_t off, i
                                            const Real *__restrict__ bx, const Real *__restrict__ by,
                                            const Real *__restrict__ bz, Real *__restrict__ Bx, Real *__restrict__ By,
                                            Real *__restrict__ Bz) {
-    auto I = [&](int ii, int jj, int kk) -> size_t {
-        return off + (size_t)wrapi(ii, nx) + (size_t)nx * ((size_t)wrapi(jj, ny) + (size_t)ny * (size_t)wrapi(kk, nz));
-    };
-    const size_t p = I(i, j, k);
+    // the cell and its periodic neighbours as offsets from it (one 64-bit
+    // index, small integer offsets)
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long p = (long long)off + i + sy * j + sz * k;
+    const long long xm2 = wrapi(i - 2, nx) - i, xm1 = wrapi(i - 1, nx) - i, xp1 = wrapi(i + 1, nx) - i;
+    const long long ym2 = (wrapi(j - 2, ny) - j) * sy, ym1 = (wrapi(j - 1, ny) - j) * sy, yp1 = (wrapi(j + 1, ny) - j) * sy;
+    const long long zm2 = (wrapi(k - 2, nz) - k) * sz, zm1 = (wrapi(k - 1, nz) - k) * sz, zp1 = (wrapi(k + 1, nz) - k) * sz;
     const Real s = Real(1.0 / 16.0);
-    Bx[p] = (Real(9) * (bx[I(i - 1, j, k)] + bx[p]) - (bx[I(i - 2, j, k)] + bx[I(i + 1, j, k)])) * s;
-    By[p] = (Real(9) * (by[I(i, j - 1, k)] + by[p]) - (by[I(i, j - 2, k)] + by[I(i, j + 1, k)])) * s;
-    Bz[p] = (Real(9) * (bz[I(i, j, k - 1)] + bz[p]) - (bz[I(i, j, k - 2)] + bz[I(i, j, k + 1)])) * s;
+    Bx[p] = (Real(9) * (bx[p + xm1] + bx[p]) - (bx[p + xm2] + bx[p + xp1])) * s;
+    By[p] = (Real(9) * (by[p + ym1] + by[p]) - (by[p + ym2] + by[p + yp1])) * s;
+    Bz[p] = (Real(9) * (bz[p + zm1] + bz[p]) - (bz[p + zm2] + bz[p + zp1])) * s;
 }
 
 template <typename Real>
@@ -265,11 +268,12 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
     const int im = i > 0 ? i - 1 : nx - 1, ip = i + 1 < nx ? i + 1 : 0;
     const int jm = j > 0 ? j - 1 : ny - 1, jp = j + 1 < ny ? j + 1 : 0;
     const int km = k > 0 ? k - 1 : nz - 1, kp = k + 1 < nz ? k + 1 : 0;
-    const size_t off = ug.off;
-    auto I = [&](int ii, int jj, int kk) -> size_t {
-        return off + (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * (size_t)kk);
-    };
-    const size_t p = I(i, j, k);
+    // the cell and its periodic neighbours as offsets from it (one 64-bit
+    // index, offsets per axis that add independently)
+    const long long sy = nx, sz = (long long)nx * ny;
+    const long long p = (long long)ug.off + i + sy * j + sz * k;
+    const long long xm = im - i, xp = ip - i, ym = (jm - j) * sy, yp = (jp - j) * sy, zm = (km - k) * sz,
+                    zp = (kp - k) * sz;
     constexpr double c = StageW<STAGE>::c, wc = StageW<STAGE>::wc;
 
     // Every load of this thread is issued before its first store, so that
@@ -279,7 +283,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
     // ---- flux divergence (Eq. num) of the five conserved fields
     Real D[5];
     {
-        const size_t pxm = I(im, j, k), pym = I(i, jm, k), pzm = I(i, j, km);
+        const long long pxm = p + xm, pym = p + ym, pzm = p + zm;
 #pragma unroll
         for (int f = 0; f < 5; ++f)
             D[f] = (a.Fx[f][pxm] - a.Fx[f][p]) * ug.rdx + (a.Fy[f][pym] - a.Fy[f][p]) * ug.rdy +
@@ -289,27 +293,28 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
     // ---- corner EMFs (Eqs. ox1-ox3) from the transport fluxes
     const Real *fy = a.Sx[0], *fz = a.Sx[1], *gz = a.Sy[0], *gx = a.Sy[1], *hx = a.Sz[0], *hy = a.Sz[1];
     const Real h = Real(0.5);
-    // Omega_x at (ii+1/2, jj+1/2, k): g*_x averaged over i, f*_y over j
-    auto Ox = [&](int ii, int iip, int jj, int jjp, int kk) -> Real {
-        return h * (gx[I(ii, jj, kk)] + gx[I(iip, jj, kk)]) - h * (fy[I(ii, jj, kk)] + fy[I(ii, jjp, kk)]);
+    // Omega_x at the edge of cell q: g*_x averaged over x (q, q + dx), f*_y
+    // over y (q, q + dy)
+    auto Ox = [&](long long q, long long dx, long long dy) -> Real {
+        return h * (gx[q] + gx[q + dx]) - h * (fy[q] + fy[q + dy]);
     };
-    // Omega_y at (i, jj+1/2, kk+1/2): h*_y averaged over j, g*_z over k
-    auto Oy = [&](int ii, int jj, int jjp, int kk, int kkp) -> Real {
-        return h * (hy[I(ii, jj, kk)] + hy[I(ii, jjp, kk)]) - h * (gz[I(ii, jj, kk)] + gz[I(ii, jj, kkp)]);
+    // Omega_y: h*_y averaged over y, g*_z over z
+    auto Oy = [&](long long q, long long dy, long long dz) -> Real {
+        return h * (hy[q] + hy[q + dy]) - h * (gz[q] + gz[q + dz]);
     };
-    // Omega_z at (ii+1/2, j, kk+1/2): f*_z averaged over k, h*_x over i
-    auto Oz = [&](int ii, int iip, int jj, int kk, int kkp) -> Real {
-        return h * (fz[I(ii, jj, kk)] + fz[I(ii, jj, kkp)]) - h * (hx[I(ii, jj, kk)] + hx[I(iip, jj, kk)]);
+    // Omega_z: f*_z averaged over z, h*_x over x
+    auto Oz = [&](long long q, long long dz, long long dx) -> Real {
+        return h * (fz[q] + fz[q + dz]) - h * (hx[q] + hx[q + dx]);
     };
-    const Real ox_c = Ox(i, ip, j, jp, k);          // Omega_x(i, j, k)
-    const Real ox_jm = Ox(i, ip, jm, j, k);         // Omega_x(i, j-1, k)
-    const Real ox_im = Ox(im, i, j, jp, k);         // Omega_x(i-1, j, k)
-    const Real oy_c = Oy(i, j, jp, k, kp);          // Omega_y(i, j, k)
-    const Real oy_km = Oy(i, j, jp, km, k);         // Omega_y(i, j, k-1)
-    const Real oy_jm = Oy(i, jm, j, k, kp);         // Omega_y(i, j-1, k)
-    const Real oz_c = Oz(i, ip, j, k, kp);          // Omega_z(i, j, k)
-    const Real oz_km = Oz(i, ip, j, km, k);         // Omega_z(i, j, k-1)
-    const Real oz_im = Oz(im, i, j, k, kp);         // Omega_z(i-1, j, k)
+    const Real ox_c = Ox(p, xp, yp);                // Omega_x(i, j, k)
+    const Real ox_jm = Ox(p + ym, xp, -ym);         // Omega_x(i, j-1, k)
+    const Real ox_im = Ox(p + xm, -xm, yp);         // Omega_x(i-1, j, k)
+    const Real oy_c = Oy(p, yp, zp);                // Omega_y(i, j, k)
+    const Real oy_km = Oy(p + zm, yp, -zm);         // Omega_y(i, j, k-1)
+    const Real oy_jm = Oy(p + ym, -ym, zp);         // Omega_y(i, j-1, k)
+    const Real oz_c = Oz(p, zp, xp);                // Omega_z(i, j, k)
+    const Real oz_km = Oz(p + zm, -zm, xp);         // Omega_z(i, j, k-1)
+    const Real oz_im = Oz(p + xm, zp, -xm);         // Omega_z(i-1, j, k)
 
     // ---- accumulators of this cell
     double accv[5];
@@ -354,14 +359,14 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
         // accumulated EMFs sum_k w'_k Omega_k, in double, at the nine edges
         const double *Ax = a.oacc[0], *Ay = a.oacc[1], *Az = a.oacc[2];
         const double ax_c = Ax[p] + wc * (double)ox_c;
-        const double ax_jm = Ax[I(i, jm, k)] + wc * (double)ox_jm;
-        const double ax_im = Ax[I(im, j, k)] + wc * (double)ox_im;
+        const double ax_jm = Ax[p + ym] + wc * (double)ox_jm;
+        const double ax_im = Ax[p + xm] + wc * (double)ox_im;
         const double ay_c = Ay[p] + wc * (double)oy_c;
-        const double ay_km = Ay[I(i, j, km)] + wc * (double)oy_km;
-        const double ay_jm = Ay[I(i, jm, k)] + wc * (double)oy_jm;
+        const double ay_km = Ay[p + zm] + wc * (double)oy_km;
+        const double ay_jm = Ay[p + ym] + wc * (double)oy_jm;
         const double az_c = Az[p] + wc * (double)oz_c;
-        const double az_km = Az[I(i, j, km)] + wc * (double)oz_km;
-        const double az_im = Az[I(im, j, k)] + wc * (double)oz_im;
+        const double az_km = Az[p + zm] + wc * (double)oz_km;
+        const double az_im = Az[p + xm] + wc * (double)oz_im;
         const double dbx = -(ax_c - ax_jm) * ug.drdy + (az_c - az_km) * ug.drdz;
         const double dby = -(ay_c - ay_km) * ug.drdz + (ax_c - ax_im) * ug.drdx;
         const double dbz = -(az_c - az_im) * ug.drdx + (ay_c - ay_jm) * ug.drdy;
