@@ -168,10 +168,26 @@ def kernel_source_hash():
 SWEEP_TRAFFIC = {"src": "3d6953991169c151", "fp64": 104.58, "fp32": 44.57}
 
 
+def hbm_gbs(traffic, launch_ms):
+    """Achieved DRAM bandwidth of a launch moving `traffic` bytes (None when
+    the traffic is unknown)."""
+    return None if traffic is None else traffic / (launch_ms * 1e-3) / 1e9
+
+
 def sweep_traffic(key, zones):
     if SWEEP_TRAFFIC.get("src") != kernel_source_hash():
         return None
     return SWEEP_TRAFFIC[key] * zones
+
+
+def conservation_drift(s, cons, bface, dx):
+    """Largest change of the eight volume totals (mass, momentum, energy,
+    face field) of a periodic run from its initial state, relative to the
+    volume integral of |state|."""
+    dv = dx[0] * dx[1] * dx[2]
+    tot0 = np.concatenate([cons.reshape(5, -1).sum(axis=1), bface.reshape(3, -1).sum(axis=1)]) * dv
+    scale = (np.abs(cons).sum() + np.abs(bface).sum()) * dv
+    return float(np.abs(s.conserved_totals() - tot0).max() / scale)
 
 
 def l1_error(a_cons, a_b, b_cons, b_b):
@@ -315,6 +331,7 @@ def run_native(args):
     b64 = torch.empty_like(bface_d)
     w5.w5ct_get_state(s64.ctx, c64, b64, None, 1)
     divb64 = s64.div_b_norm()[0]
+    drift64 = conservation_drift(s64, cons, bface, dx)
     s64.close()
 
     # ---- FP32-bulk
@@ -329,6 +346,7 @@ def run_native(args):
     b32 = torch.empty_like(bface_d)
     w5.w5ct_get_state(s32.ctx, c32, b32, None, 1)
     divb32 = s32.div_b_norm()[0]
+    drift32 = conservation_drift(s32, cons, bface, dx)
     s32.close()
     c64h, b64h, c32h, b32h = (t.cpu().numpy() for t in (c64, b64, c32, b32))
     l1 = l1_error(c32h, b32h, c64h, b64h)
@@ -396,6 +414,8 @@ def run_native(args):
                      "unit": "TFLOP/s", "frac": ach64 / PEAK_FP64_TFLOPS,
                      "traffic": sweep_traffic("fp64", zones), "launch_ms": swms64 / nsw64,
                      "algorithmic_flops_per_launch": sweep_flops,
+                     "hbm_gbs": hbm_gbs(sweep_traffic("fp64", zones), swms64 / nsw64),
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
                      "step_tflops": STEP_FLOPS_PER_ZONE * value64 / world / 1e12,
                      "peak_source": "GB300 FP64 unit count: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz = 1.26; "
                                     "published 1.25 TFLOP/s (probe measured 1.0 TFLOP/s DFMA)"},
@@ -403,10 +423,12 @@ def run_native(args):
             "value": value32, "unit": "zone-updates/s", "ms_per_step": ms32 / args.steps, "dtype": "f32",
             "accumulate": "f64", "speedup_vs_fp64": value32 / value64,
             "l1_vs_fp64": l1, "l1_fp64_change": l1_ref, "max_rel_vs_fp64": relmax, "div_b_linf": divb32,
+            "conservation_drift": drift32,
             "error_steps": nlog,
             "roofline": {"kernel": "sweep_kernel (FP32)", "bound": "alu", "achieved": ach32,
                          "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
                          "traffic": sweep_traffic("fp32", zones), "launch_ms": swms32 / nsw32,
+                         "hbm_gbs": hbm_gbs(sweep_traffic("fp32", zones), swms32 / nsw32),
                          "step_tflops": STEP_FLOPS_PER_ZONE * value32 / world / 1e12,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "gpu_launches": launches32,
@@ -416,6 +438,7 @@ def run_native(args):
                     "fp32_bulk_value": replica_throughput(world, zones, args.steps, msfjs),
                     "fp32_bulk_ms_per_step": msfjs / args.steps},
         "div_b_linf": divb64,
+        "conservation_drift": drift64,
         "e2e": {"value": world * zones * e2e_steps / e2e_s, "unit": "zone-updates/s",
                 "h2d_bytes_per_step": int(cons.nbytes + bface.nbytes),
                 "d2h_bytes_per_step": int(cons.nbytes + bface.nbytes), "steps": e2e_steps},
