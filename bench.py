@@ -615,6 +615,9 @@ def run_wave(args):
     print(json.dumps(line))
 
 
+SCHEDULES = ["one launch per kernel", "persistent sweeps per tile variant", "whole step in one persistent launch"]
+
+
 def _patch_state_job(spec):
     from paper_1812_04278_gb300 import inputs
     return inputs.patch_state(spec)
@@ -687,12 +690,16 @@ def run_batched(args):
     tune_s = time.perf_counter() - t0
     tiles_tuned = b32.tile_variants().tolist()
     schedule = b32.schedule()
-    # the other schedule, for the record
-    b32.set_schedule(1 - schedule)
-    reset(b32)
-    b32.step_graph(args.warmup)
-    torch.cuda.synchronize()
-    ms_other = graph_steps(b32, args.steps)
+    # every schedule, for the record
+    ms_sched = {}
+    for sc in (0, 1, 2):
+        b32.set_schedule(sc)
+        reset(b32)
+        b32.step_graph(args.warmup)
+        torch.cuda.synchronize()
+        ms_sched[sc] = graph_steps(b32, args.steps)
+        if b32.status()[1]:
+            ms_sched[sc] = float("nan")
     b32.set_schedule(schedule)
     reset(b32)
     b32.step_graph(args.warmup)
@@ -704,14 +711,17 @@ def run_batched(args):
     clocks = sampler.stop()
     launches = w5.w5ct_launch_count(b32.ctx) - launches0
     hits, bad = b32.status()
-    # per-launch time of the sweeps (eager steps with the launch timers on)
+    # per-launch time of the sweeps (eager steps with the launch timers on,
+    # one launch per axis and variant)
     reset(b32)
+    b32.set_schedule(0)
     w5.w5ct_set_timing(b32.ctx, True)
     for _ in range(2):
         b32.step_cfl()
     torch.cuda.synchronize()
     nsw, swms = w5.w5ct_sweep_timing(b32.ctx)
     w5.w5ct_set_timing(b32.ctx, False)
+    b32.set_schedule(schedule)
     divb32 = max(b32.div_b_norm(p)[0] for p in range(npatch))
     b32.close()
 
@@ -792,8 +802,8 @@ def run_batched(args):
                   "patches_per_axis_and_variant_tuned": tiles_tuned,
                   "patches_per_axis_and_variant_model": tiles_model,
                   "model_value": zones * args.steps / (ms_model * 1e-3), "autotune_seconds": tune_s,
-                  "schedule": ["one launch per axis and variant", "persistent work queue per variant"][schedule],
-                  "other_schedule_value": zones * args.steps / (ms_other * 1e-3)},
+                  "schedule": SCHEDULES[schedule],
+                  "schedule_values": {SCHEDULES[k]: zones * args.steps / (v * 1e-3) for k, v in ms_sched.items()}},
         "unbatched_fp32": {"value": zones * nu / (msu * 1e-3), "ms_per_step": msu / nu, "steps": nu,
                            "contexts": npatch},
         "floor_hits": hits, "nonphysical": bad + bad_model, "div_b_linf": divb32,

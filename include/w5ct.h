@@ -50,8 +50,8 @@ extern "C" {
 #define W5CT_ERR_STATE (-3)        /* call out of order (e.g. step before set_state) */
 #define W5CT_ERR_NONPHYSICAL (-4)  /* rho <= 0, P <= 0 or NaN met inside the scheme */
 #define W5CT_ERR_UNSUPPORTED (-5)  /* valid request this build does not implement */
-#define W5CT_ERR_TIMEOUT (-6)      /* a bounded device wait expired; reserved: no kernel of
-                                      this build waits on another block or on the host */
+#define W5CT_ERR_TIMEOUT (-6)      /* a bounded device wait of the fused step expired (the
+                                      state of that step is not valid) */
 
 #define W5CT_WENO_JS 0             /* Jiang-Shu weights, eps = 1e-6 (Sec. 2.2) */
 #define W5CT_WENO_Z 1              /* WENO-Z weights (Sec. 2.2), ratio squared */
@@ -151,7 +151,8 @@ int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
  * with the same (nx, ny) (x- and y-sweeps) or (nx, nz) (z-sweep) on the
  * current state, `reps` timed launches each, and keeps the fastest per class
  * (synchronises; needs a state; the flux buffers are overwritten, counters
- * kept) and then the faster sweep schedule (w5ct_set_sweep_schedule).
+ * kept) and then the fastest step schedule (w5ct_set_sweep_schedule),
+ * timed on whole steps from a snapshot of the state that is put back.
  * mode = W5CT_TUNE_MODEL (the choice w5ct_init_grid makes) takes
  * the variant with the fewest padded lanes and rows per face.  mode = v >= 0
  * forces variant v on every patch.  A captured step graph is dropped.  With
@@ -160,18 +161,24 @@ int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
 #define W5CT_TUNE_MODEL (-2)
 int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
 
-/* Schedule of the batched sweeps (npatch > 1; no counterpart in the paper).
+/* Schedule of a batched step (npatch > 1; no counterpart in the paper).
  * 0 (the default after w5ct_init_grid): per stage, one launch per axis and
- * tile variant over all patches' tiles.  1: per stage, one persistent launch
- * per tile variant, as many blocks as fit on the device at once, each block
- * taking tiles of all three axes from a device work queue (an atomically
- * incremented counter, zeroed at the start of every step) until the list is
- * exhausted; no block waits on another.  Every face is computed from the
- * same source; the compiler may contract a few operations differently in
- * the fused kernel, so results agree to rounding (not bit for bit).
- * w5ct_autotune(W5CT_TUNE_MEASURE) also picks the faster schedule.  Changing
- * it drops a captured step graph.  W5CT_ERR_UNSUPPORTED for schedule 1 with
- * one patch. */
+ * tile variant over all patches' tiles, then one update launch.  1: per
+ * stage, one persistent launch per tile variant, as many blocks as fit on the
+ * device at once, each block taking tiles of all three axes from a device
+ * work queue (an atomically incremented counter, zeroed at the start of every
+ * step) until the list is exhausted; no block waits on another.  2: the
+ * whole step (cell fields, CFL reduction and dt, the sweeps in 32-lane tiles,
+ * the four stage updates) in one persistent launch over a work queue in
+ * which each item waits, with bounded spins, for the earlier items of its own
+ * patch that it depends on; an expired wait aborts the launch and the next
+ * synchronising call returns W5CT_ERR_TIMEOUT.  Every face and cell is
+ * computed from the same source in all schedules; the compiler may contract a
+ * few operations differently in the fused kernels, so the results agree to
+ * rounding (not bit for bit).  w5ct_autotune(W5CT_TUNE_MEASURE) times whole
+ * steps of the three and keeps the fastest.  Changing the schedule drops a
+ * captured step graph.  W5CT_ERR_UNSUPPORTED for schedules 1 and 2 with one
+ * patch. */
 int w5ct_set_sweep_schedule(w5ct_ctx *ctx, int schedule);
 int w5ct_sweep_schedule(w5ct_ctx *ctx, int *schedule);
 

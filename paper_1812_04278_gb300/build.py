@@ -13,8 +13,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libw5ct.so")
 SOURCES = ["w5ct_adjoint64z.cu", "w5ct_adjoint64js.cu", "w5ct_adjoint32z.cu", "w5ct_adjoint32js.cu",
-           "w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_noalloc.cu"]
-HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_dual.cuh", "w5ct_adjoint.cuh"]
+           "w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_fused32.cu", "w5ct_fused64.cu",
+           "w5ct_noalloc.cu"]
+HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_dual.cuh", "w5ct_adjoint.cuh",
+           "w5ct_fused.cuh"]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -23,7 +25,11 @@ CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # reciprocal / square root and flushes subnormals; every double operation
 # and every other translation unit stays IEEE.
 FAST_FLOAT = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-TU_FLAGS = {"w5ct_sweep32.cu": FAST_FLOAT, "w5ct_adjoint32z.cu": FAST_FLOAT, "w5ct_adjoint32js.cu": FAST_FLOAT}
+# The fused step kernel reads data that other blocks of the same launch
+# wrote: its global loads bypass L1 (-dlcm=cg).
+L2_ONLY = ["-Xptxas", "-dlcm=cg"]
+TU_FLAGS = {"w5ct_sweep32.cu": FAST_FLOAT, "w5ct_adjoint32z.cu": FAST_FLOAT, "w5ct_adjoint32js.cu": FAST_FLOAT,
+            "w5ct_fused32.cu": FAST_FLOAT + L2_ONLY, "w5ct_fused64.cu": L2_ONLY}
 
 
 def _newest_input() -> float:

@@ -10,6 +10,7 @@
 
 #include "w5ct.h"
 #include "w5ct_adjoint.cuh"
+#include "w5ct_fused.cuh"
 #include "w5ct_internal.h"
 
 using namespace w5ct;
@@ -59,7 +60,14 @@ struct w5ct_ctx {
     int4 *tiles_buf = nullptr;
     int seg_off[3][kMaxTileVariants] = {};
     int seg_n[3][kMaxTileVariants] = {};
-    int schedule = 0;                // batched sweeps: 0 = one launch per axis and variant, 1 = persistent
+    int schedule = 0;                // batched sweeps: 0 = one launch per axis and variant, 1 = persistent,
+                                     // 2 = the whole step in one persistent launch (fused)
+    // fused step (schedule 2): work items, per-patch targets and counters in one allocation
+    void *fused_buf = nullptr;
+    int4 *fused_items = nullptr;
+    int nfused = 0;
+    int *fused_ncb = nullptr, *fused_ntile = nullptr, *fused_done = nullptr, *fused_qa = nullptr;
+    int fused_blocks = 0;
     int pgrid[kMaxTileVariants] = {};   // resident blocks of the persistent sweep per variant
     int *pcounters = nullptr;        // work-queue counters: 4 stages x kMaxTileVariants
     long long sweep_units = 0;       // axis-sweeps covered by the timed event pairs
@@ -139,6 +147,9 @@ void free_grid(w5ct_ctx *c) {
     c->tiles_buf = nullptr;
     if (c->adj_slab) cudaFree(c->adj_slab);
     c->adj_slab = nullptr;
+    if (c->fused_buf) cudaFree(c->fused_buf);
+    c->fused_buf = nullptr;
+    c->nfused = 0;
     for (int a = 0; a < 3; ++a) c->pvar[a].clear();
     c->have_grid = false;
     c->have_state = false;
@@ -315,6 +326,174 @@ void launch_update_stage(w5ct_ctx *c, const UpdateArgs<Real> &u) {
         update_kernel<Real, S><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(u);
 }
 
+// The stage-update arguments of the context's buffers (dt from dt_dev).
+template <typename Real>
+UpdateArgs<Real> update_args(w5ct_ctx *c, const double *dt_dev) {
+    const long long n = c->n;
+    UpdateArgs<Real> u;
+    u.nx = c->nx;
+    u.ny = c->ny;
+    u.nz = c->nz;
+    u.rdx = (Real)(1.0 / c->dx);
+    u.rdy = (Real)(1.0 / c->dy);
+    u.rdz = (Real)(1.0 / c->dz);
+    u.drdx = 1.0 / c->dx;
+    u.drdy = 1.0 / c->dy;
+    u.drdz = 1.0 / c->dz;
+    for (int f = 0; f < 5; ++f) {
+        u.Fx[f] = plane<Real>(c->Fx, n, f);
+        u.Fy[f] = plane<Real>(c->Fy, n, f);
+        u.Fz[f] = plane<Real>(c->Fz, n, f);
+        u.q0[f] = c->q0 + (size_t)f * n;
+        u.acc[f] = c->acc + (size_t)f * n;
+        u.qs[f] = plane<Real>(c->qs, n, f);
+        u.q0r[f] = plane<Real>(c->q0r, n, f);
+    }
+    for (int f = 0; f < 2; ++f) {
+        u.Sx[f] = plane<Real>(c->Sx, n, f);
+        u.Sy[f] = plane<Real>(c->Sy, n, f);
+        u.Sz[f] = plane<Real>(c->Sz, n, f);
+    }
+    for (int f = 0; f < 3; ++f) {
+        u.b0[f] = c->b0 + (size_t)f * n;
+        u.oacc[f] = c->oacc + (size_t)f * n;
+        u.bs[f] = plane<Real>(c->bs, n, f);
+        u.b0r[f] = plane<Real>(c->b0r, n, f);
+    }
+    u.dt = dt_dev;
+    return u;
+}
+
+// Work items of the fused step (see w5ct_fused.cuh), the per-patch targets
+// and the counters, in one allocation; the resident-block count.
+int build_fused(w5ct_ctx *c) {
+    if (c->fused_buf) return W5CT_OK;
+    std::vector<int4> items;
+    std::vector<int> ncb(c->npatch), ntile(c->npatch, 0);
+    const bool fp64 = c->cfg.precision == W5CT_FP64;
+    const int t2x = fp64 ? sweep_t2<double>(0) : sweep_t2<float>(0);
+    const int t2yz = fp64 ? sweep_t2<double>(1) : sweep_t2<float>(1);
+    for (int p = 0; p < c->npatch; ++p) {
+        const PatchGeom &g = c->pg[p];
+        ncb[p] = (int)(((long long)g.nx * g.ny * g.nz + 255) / 256);
+    }
+    // Phase-major within a stage (every patch's cell fields, then CFL blocks
+    // and dts, then sweeps, then updates): an item's dependencies then lie a
+    // whole phase back in the queue and are usually done when it is taken.
+    for (int st = 0; st < 4; ++st) {
+        for (int p = 0; p < c->npatch; ++p)
+            for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_CELLB, st, 0, 0), q * 256, 0));
+        if (st == 0) {
+            for (int p = 0; p < c->npatch; ++p)
+                for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_SPEED, 0, 0, 0), q * 256, 0));
+            for (int p = 0; p < c->npatch; ++p) items.push_back(make_int4(p, fused_tag(FI_DT, 0, 0, 0), 0, 0));
+        }
+        for (int p = 0; p < c->npatch; ++p) {
+            const PatchGeom &g = c->pg[p];
+            const size_t before = items.size();
+            const int nbx = (g.nx + 31) / 32;
+            for (int k = 0; k < g.nz; ++k)
+                for (int j = 0; j < (g.ny + t2x - 1) / t2x; ++j)
+                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 0, i), j, k));
+            for (int k = 0; k < g.nz; ++k)
+                for (int j = 0; j < (g.ny + t2yz - 1) / t2yz; ++j)
+                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 1, i), j, k));
+            for (int k = 0; k < (g.nz + t2yz - 1) / t2yz; ++k)
+                for (int j = 0; j < g.ny; ++j)
+                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 2, i), j, k));
+            if (st == 0) ntile[p] = (int)(items.size() - before);
+        }
+        for (int p = 0; p < c->npatch; ++p)
+            for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_UPDATE, st, 0, 0), q * 256, 0));
+    }
+    if (items.size() > (size_t)0x7fffffff) return fail(c, W5CT_ERR_ARG, "too many work items for the fused step");
+    const size_t P = (size_t)c->npatch;
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
+    const size_t o_it = take(sizeof(int4) * items.size()), o_ncb = take(sizeof(int) * P), o_nt = take(sizeof(int) * P);
+    const size_t o_done = take(sizeof(int) * 14 * P), o_qa = take(sizeof(int) * 2);
+    W5_CUDA(c, cudaMalloc(&c->fused_buf, bytes));
+    char *b = (char *)c->fused_buf;
+    c->fused_items = (int4 *)(b + o_it);
+    c->fused_ncb = (int *)(b + o_ncb);
+    c->fused_ntile = (int *)(b + o_nt);
+    c->fused_done = (int *)(b + o_done);
+    c->fused_qa = (int *)(b + o_qa);
+    c->nfused = (int)items.size();
+    W5_CUDA(c, cudaMemcpy(c->fused_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    W5_CUDA(c, cudaMemcpy(c->fused_ncb, ncb.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    W5_CUDA(c, cudaMemcpy(c->fused_ntile, ntile.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
+    size_t smem = 0;
+    const cudaError_t e = fp64 ? fused_grid<double>(c->cfg.weno_variant, c->fused_blocks, smem)
+                               : fused_grid<float>(c->cfg.weno_variant, c->fused_blocks, smem);
+    W5_CUDA(c, e);
+    return W5CT_OK;
+}
+
+// One step of every patch in one persistent launch: dts given (device,
+// npatch doubles) or, when dts_in is NULL, from each patch's CFL condition
+// (copied to dts_out when not NULL).
+template <typename Real>
+int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out) {
+    int rc = build_fused(c);
+    if (rc) return rc;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    const size_t P = (size_t)c->npatch;
+    W5_CUDA(c, cudaMemsetAsync(c->fused_done, 0, sizeof(int) * 14 * P, st));
+    W5_CUDA(c, cudaMemsetAsync(c->fused_qa, 0, sizeof(int) * 2, st));
+    if (!dts_in) W5_CUDA(c, cudaMemsetAsync(c->smax, 0, 3 * sizeof(unsigned long long) * P, st));
+    FusedArgs<Real> A;
+    void *Fax[3] = {c->Fx, c->Fy, c->Fz};
+    void *Sax[3] = {c->Sx, c->Sy, c->Sz};
+    for (int ax = 0; ax < 3; ++ax) {
+        SweepArgs<Real> &a = A.a[ax];
+        a.nx = c->nx;
+        a.ny = c->ny;
+        a.nz = c->nz;
+        for (int f = 0; f < 5; ++f) a.q[f] = plane<Real>(c->qs, n, f);
+        for (int f = 0; f < 3; ++f) a.bc[f] = plane<Real>(c->bc, n, f);
+        for (int f = 0; f < 5; ++f) a.F[f] = plane<Real>(Fax[ax], n, f);
+        for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
+        a.K = make_phys<Real>(c->cfg);
+        a.flag = c->flag;
+        a.hits = c->hits;
+    }
+    A.u = update_args<Real>(c, c->dt_dev);
+    for (int f = 0; f < 3; ++f) {
+        A.bs[f] = plane<Real>(c->bs, n, f);
+        A.bc[f] = plane<Real>(c->bc, n, f);
+    }
+    A.pgs = c->pg_dev;
+    A.items = c->fused_items;
+    A.nitems = c->nfused;
+    A.ncb = c->fused_ncb;
+    A.ntile = c->fused_ntile;
+    A.ctr.queue = c->fused_qa;
+    A.ctr.abort = c->fused_qa + 1;
+    A.ctr.done = c->fused_done;
+    A.ctr.npatch = c->npatch;
+    A.cfl = dts_in ? 0 : 1;
+    A.cfl_number = c->cfg.cfl;
+    A.dts = dts_in ? const_cast<double *>(dts_in) : c->dt_dev;
+    A.dts_out = dts_in ? nullptr : dts_out;
+    A.smax = c->smax;
+    A.spin_limit = 1LL << 22;   // x 256 ns of sleep: about a second
+    int e0 = record_event(c);
+    if (e0) return e0;
+    W5_CUDA(c, launch_fused_step<Real>(c->cfg.weno_variant, A, c->fused_blocks, st));
+    c->launches++;
+    e0 = record_event(c);
+    if (e0) return e0;
+    if (c->timing) c->sweep_units += 12;
+    return W5CT_OK;
+}
+
+int fused_step(w5ct_ctx *c, const double *dts_in, double *dts_out) {
+    return c->cfg.precision == W5CT_FP64 ? fused_step_impl<double>(c, dts_in, dts_out)
+                                         : fused_step_impl<float>(c, dts_in, dts_out);
+}
+
 // The three sweeps of a stage over every patch: schedule 0 launches one
 // kernel per axis and tile variant; schedule 1 one persistent kernel per
 // variant over the three axes' tiles, with the work-queue counters
@@ -366,37 +545,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
     a.flag = c->flag;
     a.hits = c->hits;
 
-    UpdateArgs<Real> u;
-    u.nx = c->nx;
-    u.ny = c->ny;
-    u.nz = c->nz;
-    u.rdx = (Real)(1.0 / c->dx);
-    u.rdy = (Real)(1.0 / c->dy);
-    u.rdz = (Real)(1.0 / c->dz);
-    u.drdx = 1.0 / c->dx;
-    u.drdy = 1.0 / c->dy;
-    u.drdz = 1.0 / c->dz;
-    for (int f = 0; f < 5; ++f) {
-        u.Fx[f] = plane<Real>(c->Fx, n, f);
-        u.Fy[f] = plane<Real>(c->Fy, n, f);
-        u.Fz[f] = plane<Real>(c->Fz, n, f);
-        u.q0[f] = c->q0 + (size_t)f * n;
-        u.acc[f] = c->acc + (size_t)f * n;
-        u.qs[f] = plane<Real>(c->qs, n, f);
-        u.q0r[f] = plane<Real>(c->q0r, n, f);
-    }
-    for (int f = 0; f < 2; ++f) {
-        u.Sx[f] = plane<Real>(c->Sx, n, f);
-        u.Sy[f] = plane<Real>(c->Sy, n, f);
-        u.Sz[f] = plane<Real>(c->Sz, n, f);
-    }
-    for (int f = 0; f < 3; ++f) {
-        u.b0[f] = c->b0 + (size_t)f * n;
-        u.oacc[f] = c->oacc + (size_t)f * n;
-        u.bs[f] = plane<Real>(c->bs, n, f);
-        u.b0r[f] = plane<Real>(c->b0r, n, f);
-    }
-    u.dt = dt_dev;
+    const UpdateArgs<Real> u = update_args<Real>(c, dt_dev);
 
     void *Fax[3] = {c->Fx, c->Fy, c->Fz};
     void *Sax[3] = {c->Sx, c->Sy, c->Sz};
@@ -482,6 +631,7 @@ int speeds_impl(w5ct_ctx *c, double *out) {
     rc = read_flag(c, &flag);
     if (rc) return rc;
     for (size_t d = 0; d < bits.size(); ++d) memcpy(&out[d], &bits[d], sizeof(double));
+    if (flag & 2) return fail(c, W5CT_ERR_TIMEOUT, "a wait of the fused step expired; the state is not valid");
     if (flag) return fail(c, W5CT_ERR_NONPHYSICAL, "non-physical state (rho <= 0, P <= 0 or NaN)");
     return W5CT_OK;
 }
@@ -748,6 +898,7 @@ int w5ct_get_state(w5ct_ctx *c, int patch, double *cons, double *bface, double *
     int flag = 0;
     rc = read_flag(c, &flag);
     if (rc) return rc;
+    if (flag & 2) return fail(c, W5CT_ERR_TIMEOUT, "a wait of the fused step expired; the state is not valid");
     if (flag) return fail(c, W5CT_ERR_NONPHYSICAL, "non-physical state (rho <= 0, P <= 0 or NaN) met in a step");
     return W5CT_OK;
 }
@@ -762,6 +913,7 @@ int w5ct_step(w5ct_ctx *c, double dt) {
         set_scalar_kernel<<<1, 1, 0, c->stream>>>(c->dt_dev, dt);
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
+    if (c->npatch > 1 && c->schedule == 2) return fused_step(c, c->dt_dev, nullptr);
     return step_impl(c, c->dt_dev, false);
 }
 
@@ -769,12 +921,14 @@ int w5ct_step_dev(w5ct_ctx *c, const double *dt_dev) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (!dt_dev) return fail(c, W5CT_ERR_ARG, "null dt_dev");
+    if (c->npatch > 1 && c->schedule == 2) return fused_step(c, dt_dev, nullptr);
     return step_impl(c, dt_dev, false);
 }
 
 int w5ct_step_cfl(w5ct_ctx *c, double *dt_dev_out) {
     int rc = check_ready(c);
     if (rc) return rc;
+    if (c->npatch > 1 && c->schedule == 2) return fused_step(c, nullptr, dt_dev_out);
     rc = c->cfg.precision == W5CT_FP64 ? launch_cellb<double>(c) : launch_cellb<float>(c);
     if (rc) return rc;
     rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
@@ -964,30 +1118,57 @@ int autotune_measure(w5ct_ctx *c, int reps) {
     }
     rc = build_tiles(c);
     if (rc) return rc;
-    // schedule: one launch per axis and variant, or one persistent launch per
-    // variant over the three axes (timed on the sweeps of a stage)
-    SweepArgs<Real> a3[3] = {sweep_args<Real>(c, 0), sweep_args<Real>(c, 1), sweep_args<Real>(c, 2)};
-    float best = 0.f;
+    // schedule (w5ct_set_sweep_schedule): timed on whole steps from a
+    // snapshot of the state, which is put back after every trial
     const bool timing = c->timing;
     c->timing = false;
-    for (int sc = 0; sc < 2; ++sc) {
-        float total = 0.f;
-        for (int r = 0; r <= reps; ++r) {
-            W5_CUDA(c, cudaMemsetAsync(c->pcounters, 0, 4 * kMaxTileVariants * sizeof(int), c->stream));
-            W5_CUDA(c, cudaEventRecord(e0, c->stream));
-            rc = launch_batched_sweeps<Real>(c, a3, sc, c->pcounters);
-            if (rc) break;
-            W5_CUDA(c, cudaEventRecord(e1, c->stream));
-            W5_CUDA(c, cudaEventSynchronize(e1));
-            float ms = 0.f;
-            W5_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-            if (r > 0) total += ms;       // the first launch is untimed
-        }
-        if (rc) break;
-        if (sc == 0 || total < best) {
-            best = total;
+    const size_t n = (size_t)c->n, rs = c->real_size;
+    const bool fp32 = c->cfg.precision != W5CT_FP64;
+    const size_t bq = 8 * n * 8, br = 8 * n * rs, bsnap = bq + br + (fp32 ? br : 0);
+    char *snap = nullptr;
+    if (cudaMalloc(&snap, bsnap) == cudaSuccess) {
+        auto copy_state = [&](bool save) -> cudaError_t {
+            struct { void *dev; size_t bytes; } parts[6] = {{c->q0, 5 * n * 8}, {c->b0, 3 * n * 8},
+                                                         {c->qs, 5 * n * rs}, {c->bs, 3 * n * rs},
+                                                         {fp32 ? c->q0r : nullptr, 5 * n * rs},
+                                                         {fp32 ? c->b0r : nullptr, 3 * n * rs}};
+            size_t o = 0;
+            for (auto &pt : parts) {
+                if (!pt.dev) continue;
+                cudaError_t e = save ? cudaMemcpyAsync(snap + o, pt.dev, pt.bytes, cudaMemcpyDeviceToDevice, c->stream)
+                                     : cudaMemcpyAsync(pt.dev, snap + o, pt.bytes, cudaMemcpyDeviceToDevice, c->stream);
+                if (e != cudaSuccess) return e;
+                o += pt.bytes;
+            }
+            return cudaSuccess;
+        };
+        cudaError_t e = copy_state(true);
+        float best = 0.f;
+        int best_sc = 0;
+        for (int sc = 0; sc < 3 && e == cudaSuccess && rc == W5CT_OK; ++sc) {
             c->schedule = sc;
+            if (sc == 2) {
+                rc = build_fused(c);
+                if (rc) break;
+            }
+            e = copy_state(false);
+            if (e == cudaSuccess) rc = w5ct_step_cfl(c, nullptr);          // untimed
+            if (e == cudaSuccess && rc == W5CT_OK) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps && e == cudaSuccess && rc == W5CT_OK; ++r) rc = w5ct_step_cfl(c, nullptr);
+            if (e == cudaSuccess && rc == W5CT_OK) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess && rc == W5CT_OK) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess && rc == W5CT_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rc == W5CT_OK && (sc == 0 || ms < best)) {
+                best = ms;
+                best_sc = sc;
+            }
         }
+        if (e == cudaSuccess) e = copy_state(false);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(snap);
+        c->schedule = best_sc;
+        if (e != cudaSuccess && rc == W5CT_OK) rc = fail(c, W5CT_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
     }
     c->timing = timing;
     cudaEventDestroy(e0);
@@ -1129,9 +1310,13 @@ int w5ct_autotune(w5ct_ctx *c, int mode, int reps) {
 int w5ct_set_sweep_schedule(w5ct_ctx *c, int schedule) {
     if (!c) return W5CT_ERR_ARG;
     if (!c->have_grid) return fail(c, W5CT_ERR_STATE, "no grid: call w5ct_init_grid first");
-    if (schedule != 0 && schedule != 1) return fail(c, W5CT_ERR_ARG, "schedule must be 0 or 1");
-    if (schedule == 1 && c->npatch == 1)
-        return fail(c, W5CT_ERR_UNSUPPORTED, "the persistent sweep schedule takes a batch of patches");
+    if (schedule < 0 || schedule > 2) return fail(c, W5CT_ERR_ARG, "schedule must be 0, 1 or 2");
+    if (schedule != 0 && c->npatch == 1)
+        return fail(c, W5CT_ERR_UNSUPPORTED, "the persistent schedules take a batch of patches");
+    if (schedule == 2) {
+        int rc = build_fused(c);
+        if (rc) return rc;
+    }
     if (c->schedule != schedule && c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1294,7 +1479,7 @@ int w5ct_status(w5ct_ctx *c, long long *floor_hits, int *nonphysical) {
     int rc = read_flag(c, &f);
     if (rc) return rc;
     if (floor_hits) *floor_hits = (long long)h;
-    if (nonphysical) *nonphysical = f;
+    if (nonphysical) *nonphysical = f & 1;
     return W5CT_OK;
 }
 

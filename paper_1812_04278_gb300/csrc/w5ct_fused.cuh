@@ -1,0 +1,273 @@
+// w5ct_fused.cuh -- one RK4 + CT step of every patch of a batch in a single
+// persistent launch (the fused schedule of the batched path).
+//
+// The step is a list of work items, built on the host: per stage s and patch
+// p, the 256-cell blocks of p's cell field (Sec. 2.3), at s = 0 the blocks of
+// p's CFL reduction (Eq. cfl) and p's dt, the sweep tiles of p along x, y and
+// z (Sec. 2.2), and the blocks of p's stage update (Eq. num, Sec. 2.1, Eqs.
+// ox1-ox3).  Each block of the persistent grid takes the next item from a
+// device counter and first waits until the items it depends on -- all of
+// them earlier in the list and all of the same patch -- are done:
+//
+//   cell field (p, s > 0)  after the update (p, s - 1)
+//   CFL blocks (p)         after the cell field (p, 0)
+//   dt (p)                 after the CFL blocks (p)
+//   sweep tiles (p, s)     after the cell field (p, s)
+//   update (p, s)          after the sweep tiles (p, s) and, at s = 0, dt (p)
+//
+// A dependency is always dequeued before the item that waits on it, by a
+// block that is running, and waits only point backwards in the list, so the
+// chain of waits ends at an item that can finish: the launch completes
+// without any assumption on how many blocks are resident.  Every wait is
+// bounded (an iteration limit with a short sleep): on expiry the block sets
+// bit 2 of the context's flag and an abort word that makes every other block
+// stop, and the step reports W5CT_ERR_TIMEOUT.
+//
+// Memory ordering: a block publishes an item with __syncthreads, a fence and
+// an atomicAdd on the item's counter; a waiter spins on the counter, fences,
+// and releases its threads with __syncthreads (the grid-synchronisation
+// pattern).  The translation units of this kernel are compiled with global
+// loads cached in L2 only (-dlcm=cg), so no block reads a line left in its
+// SM's L1 by an earlier item.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "w5ct_internal.h"
+
+namespace w5ct {
+
+enum FusedItem { FI_CELLB = 0, FI_SPEED = 1, FI_DT = 2, FI_SWEEP = 3, FI_UPDATE = 4 };
+
+// item: x = patch, y = type | stage << 3 | axis << 5 | tbx << 8, z, w =
+// (tby, tbz) of a sweep tile or (first cell, 0) of a cell block
+__host__ __device__ inline int fused_tag(int type, int stage, int axis, int tbx) {
+    return type | (stage << 3) | (axis << 5) | (tbx << 8);
+}
+
+// Per-patch completion counters, zeroed at the start of every step:
+// cellb[s][p], sweep[s][p], update[s][p], speed[p], dt[p].
+struct FusedCounters {
+    int *queue;      // next item
+    int *abort;      // set when a wait expires
+    int *done;       // 14 * npatch counters
+    int npatch;
+    __device__ int *cellb(int s, int p) const { return done + s * npatch + p; }
+    __device__ int *sweep(int s, int p) const { return done + (4 + s) * npatch + p; }
+    __device__ int *update(int s, int p) const { return done + (8 + s) * npatch + p; }
+    __device__ int *speed(int p) const { return done + 12 * npatch + p; }
+    __device__ int *dtc(int p) const { return done + 13 * npatch + p; }
+};
+
+template <typename Real>
+struct FusedArgs {
+    SweepArgs<Real> a[3];        // sweeps along x, y, z (flux outputs per axis)
+    UpdateArgs<Real> u;          // stage update (u.dt unused: dts below)
+    const Real *bs[3];           // stage face field -> cell field a[*].bc
+    Real *bc[3];
+    const PatchGeom *pgs;
+    const int4 *items;
+    int nitems;
+    const int *ncb;              // cell blocks per patch
+    const int *ntile;            // sweep tiles (three axes) per patch
+    FusedCounters ctr;
+    int cfl;                     // 1: dt of each patch from its state; 0: dts given
+    double cfl_number;
+    double *dts;                 // per-patch dt (written when cfl, read by the updates)
+    double *dts_out;             // optional copy of the dts
+    unsigned long long *smax;    // 3 per patch, zeroed before the launch
+    long long spin_limit;
+};
+
+// thread 0 of a block: wait until *ctr >= target; false if aborted or expired
+__device__ __forceinline__ bool fused_wait(const FusedCounters &C, const int *ctr, int target, long long limit,
+                                           int *flag) {
+    long long it = 0;
+    for (;;) {
+        const int v = *(volatile const int *)ctr;
+        if (v >= target) {
+            __threadfence();
+            return true;
+        }
+        if (*(volatile const int *)C.abort) return false;
+        if (++it > limit) {
+            atomicExch(C.abort, 1);
+            atomicOr(flag, 2);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+// the cell-centred field of one cell (Sec. 2.3), plain loads
+template <typename Real>
+__device__ __forceinline__ void fused_cellb(const PatchGeom &g, int i, int j, int k, const Real *bx, const Real *by,
+                                            const Real *bz, Real *Bx, Real *By, Real *Bz) {
+    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+    const long long p = g.off + i + sy * j + sz * k;
+    const long long xm2 = wrapi(i - 2, g.nx) - i, xm1 = wrapi(i - 1, g.nx) - i, xp1 = wrapi(i + 1, g.nx) - i;
+    const long long ym2 = (wrapi(j - 2, g.ny) - j) * sy, ym1 = (wrapi(j - 1, g.ny) - j) * sy,
+                    yp1 = (wrapi(j + 1, g.ny) - j) * sy;
+    const long long zm2 = (wrapi(k - 2, g.nz) - k) * sz, zm1 = (wrapi(k - 1, g.nz) - k) * sz,
+                    zp1 = (wrapi(k + 1, g.nz) - k) * sz;
+    const Real s = Real(1.0 / 16.0);
+    Bx[p] = (Real(9) * (bx[p + xm1] + bx[p]) - (bx[p + xm2] + bx[p + xp1])) * s;
+    By[p] = (Real(9) * (by[p + ym1] + by[p]) - (by[p + ym2] + by[p + yp1])) * s;
+    Bz[p] = (Real(9) * (bz[p + zm1] + bz[p]) - (bz[p + zm2] + bz[p + zp1])) * s;
+}
+
+template <typename Real, int VAR>
+__global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kernel(FusedArgs<Real> A) {
+    extern __shared__ __align__(16) unsigned char w5ct_smem[];
+    __shared__ int s_item, s_ok;
+    __shared__ double s_red[3 * 32];
+    Real *sm = reinterpret_cast<Real *>(w5ct_smem);
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const FusedCounters &C = A.ctr;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(C.queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= A.nitems) break;
+        const int4 t = A.items[it];
+        const int p = t.x;
+        const int type = t.y & 7, stage = (t.y >> 3) & 3, axis = (t.y >> 5) & 3, tbx = t.y >> 8;
+        const PatchGeom pg = A.pgs[p];
+        // ---- wait for this item's dependencies (thread 0), then release the block
+        if (tid == 0) {
+            bool ok = true;
+            switch (type) {
+                case FI_CELLB:
+                    if (stage > 0) ok = fused_wait(C, C.update(stage - 1, p), A.ncb[p], A.spin_limit, A.a[0].flag);
+                    break;
+                case FI_SPEED: ok = fused_wait(C, C.cellb(0, p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
+                case FI_DT: ok = fused_wait(C, C.speed(p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
+                case FI_SWEEP: ok = fused_wait(C, C.cellb(stage, p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
+                default:
+                    ok = fused_wait(C, C.sweep(stage, p), A.ntile[p], A.spin_limit, A.a[0].flag);
+                    if (ok && stage == 0) ok = fused_wait(C, C.dtc(p), 1, A.spin_limit, A.a[0].flag);
+                    break;
+            }
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        // ---- the item's work
+        int *done = nullptr;
+        if (type == FI_SWEEP) {
+            if (axis == 0)
+                sweep_tile<0, Real, VAR, SweepTuning<Real>::T2X>(A.a[0], pg, tbx, t.z, t.w, sm);
+            else if (axis == 1)
+                sweep_tile<1, Real, VAR, SweepTuning<Real>::T2YZ>(A.a[1], pg, tbx, t.z, t.w, sm);
+            else
+                sweep_tile<2, Real, VAR, SweepTuning<Real>::T2YZ>(A.a[2], pg, tbx, t.z, t.w, sm);
+            done = C.sweep(stage, p);
+        } else if (type == FI_DT) {
+            if (tid == 0 && A.cfl) {
+                const double s0 = __longlong_as_double((long long)A.smax[3 * p + 0]);
+                const double s1 = __longlong_as_double((long long)A.smax[3 * p + 1]);
+                const double s2 = __longlong_as_double((long long)A.smax[3 * p + 2]);
+                const double sum = __dadd_rn(__dadd_rn(__ddiv_rn(s0, pg.dx), __ddiv_rn(s1, pg.dy)), __ddiv_rn(s2, pg.dz));
+                const double v = __ddiv_rn(A.cfl_number, sum);
+                A.dts[p] = v;
+                if (A.dts_out) A.dts_out[p] = v;
+            }
+            done = C.dtc(p);
+        } else {
+            // a block of 256 consecutive cells of the patch
+            const int idx = t.z + tid;
+            const bool in = idx < pg.nx * pg.ny * pg.nz;
+            const int row = idx / pg.nx;
+            const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
+            if (type == FI_CELLB) {
+                if (in) fused_cellb<Real>(pg, i, j, k, A.bs[0], A.bs[1], A.bs[2], A.bc[0], A.bc[1], A.bc[2]);
+                done = C.cellb(stage, p);
+            } else if (type == FI_SPEED) {
+                if (A.cfl) {
+                    double v[3] = {0.0, 0.0, 0.0};
+                    bool bad = false;
+                    if (in) {
+                        const size_t q = (size_t)pg.off + (size_t)idx;
+                        const SweepArgs<Real> &a = A.a[0];
+                        cell_speeds<Real>(a.q[0][q], a.q[1][q], a.q[2][q], a.q[3][q], a.q[4][q], a.bc[0][q],
+                                          a.bc[1][q], a.bc[2][q], a.K, v, bad);
+                    }
+                    if (bad) atomicOr(A.a[0].flag, 1);
+                    // maxima over the block's eight warps
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v[d] = fmax(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+                    if ((tid & 31) == 0)
+                        for (int d = 0; d < 3; ++d) s_red[d * 32 + (tid >> 5)] = v[d];
+                    __syncthreads();
+                    if (tid < 32) {
+                        for (int d = 0; d < 3; ++d) {
+                            double x = tid < 8 ? s_red[d * 32 + tid] : 0.0;
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+                            if (tid == 0) atomicMax(&A.smax[3 * p + d], (unsigned long long)__double_as_longlong(x));
+                        }
+                    }
+                }
+                done = C.speed(p);
+            } else {
+                if (in) {
+                    const UpdGeom<Real> ug = {pg.nx, pg.ny, pg.nz, (size_t)pg.off, (Real)pg.rdx, (Real)pg.rdy,
+                                              (Real)pg.rdz, pg.rdx, pg.rdy, pg.rdz};
+                    const double dt = A.dts[p];
+                    switch (stage) {
+                        case 0: update_cell<Real, 0>(A.u, ug, i, j, k, dt); break;
+                        case 1: update_cell<Real, 1>(A.u, ug, i, j, k, dt); break;
+                        case 2: update_cell<Real, 2>(A.u, ug, i, j, k, dt); break;
+                        default: update_cell<Real, 3>(A.u, ug, i, j, k, dt); break;
+                    }
+                }
+                done = C.update(stage, p);
+            }
+        }
+        // ---- publish: every thread's writes, then the counter
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(done, 1);
+        }
+    }
+}
+
+// Defined in w5ct_fused32.cu / w5ct_fused64.cu.
+template <typename Real>
+cudaError_t launch_fused_step(int variant, const FusedArgs<Real> &A, int blocks, cudaStream_t s);
+template <typename Real>
+cudaError_t fused_grid(int variant, int &blocks, size_t &smem);
+
+template <typename Real, int VAR>
+size_t fused_smem() {
+    using T0 = SweepTile<0, SweepTuning<Real>::T2X>;
+    using T1 = SweepTile<1, SweepTuning<Real>::T2YZ>;
+    using T2_ = SweepTile<2, SweepTuning<Real>::T2YZ>;
+    size_t m = (size_t)T0::NC;
+    if ((size_t)T1::NC > m) m = (size_t)T1::NC;
+    if ((size_t)T2_::NC > m) m = (size_t)T2_::NC;
+    return m * NCQ * sizeof(Real);
+}
+
+template <typename Real, int VAR>
+cudaError_t fused_grid_impl(int &blocks, size_t &smem) {
+    smem = fused_smem<Real, VAR>();
+    cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<Real, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    int dev = 0, sms = 0, per = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fused_step_kernel<Real, VAR>, 256, smem);
+    blocks = sms * (per > 0 ? per : 1);
+    return e;
+}
+
+template <typename Real, int VAR>
+cudaError_t launch_fused_impl(const FusedArgs<Real> &A, int blocks, cudaStream_t s) {
+    fused_step_kernel<Real, VAR><<<blocks, dim3(32, 8), fused_smem<Real, VAR>(), s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace w5ct

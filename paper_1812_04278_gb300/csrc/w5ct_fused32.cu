@@ -1,0 +1,18 @@
+// w5ct_fused32.cu -- the fused persistent step kernel for Real = float (one
+// translation unit per arithmetic type, compiled with global loads cached in
+// L2 only; see w5ct_fused.cuh).
+#include "w5ct_fused.cuh"
+
+namespace w5ct {
+
+template <>
+cudaError_t launch_fused_step<float>(int variant, const FusedArgs<float> &A, int blocks, cudaStream_t s) {
+    return variant == 0 ? launch_fused_impl<float, 0>(A, blocks, s) : launch_fused_impl<float, 1>(A, blocks, s);
+}
+
+template <>
+cudaError_t fused_grid<float>(int variant, int &blocks, size_t &smem) {
+    return variant == 0 ? fused_grid_impl<float, 0>(blocks, smem) : fused_grid_impl<float, 1>(blocks, smem);
+}
+
+}  // namespace w5ct

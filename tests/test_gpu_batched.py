@@ -193,6 +193,7 @@ def test_tile_variants_do_not_change_results(env, single_fp32, mode):
     sts, dt, ref = single_fp32
     b = make_batch(env, SHAPES, sts, 1, 1)
     b.autotune(mode, 2)
+    b.set_schedule(0)          # the schedules agree only to rounding (tested below)
     counts = b.tile_variants()
     assert counts.sum(axis=1).tolist() == [len(SHAPES)] * 3
     if mode >= 0:
@@ -260,7 +261,70 @@ def test_persistent_schedule_gives_the_same_results(env, single_fp32, precision,
 def test_persistent_schedule_needs_a_batch(env):
     W, torch = env["W"], env["torch"]
     s = W.Solver((8, 8, 8), 0.125, W.make_config(), stream=torch.cuda.current_stream().cuda_stream)
+    for sched in (1, 2):
+        with pytest.raises(W.W5ctError) as e:
+            W.w5ct_set_sweep_schedule(s.ctx, sched)
+        assert e.value.code == W.W5CT_ERR_UNSUPPORTED
     with pytest.raises(W.W5ctError) as e:
-        W.w5ct_set_sweep_schedule(s.ctx, 1)
-    assert e.value.code == W.W5CT_ERR_UNSUPPORTED
+        W.w5ct_set_sweep_schedule(s.ctx, 3)
+    assert e.value.code == W.W5CT_ERR_ARG
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fused_step_agrees_with_launch_per_kernel(env, precision, variant):
+    """Schedule 2 (the whole step in one persistent launch over a work queue
+    with per-patch dependencies) gives the states and per-patch dts of the
+    launch-per-kernel schedule, through every step entry point and a graph
+    replay; no wait expires."""
+    torch = env["torch"]
+    sts = states(env, SHAPES, 1100 + 10 * precision + variant)
+    a = make_batch(env, SHAPES, sts, precision, variant)
+    b = make_batch(env, SHAPES, sts, precision, variant)
+    b.set_schedule(2)
+    assert b.schedule() == 2
+    da = torch.zeros(len(SHAPES), dtype=torch.float64, device="cuda")
+    db = torch.zeros_like(da)
+    a.step_cfl(da)
+    b.step_cfl(db)
+    if precision == 0:
+        assert torch.equal(da, db)                 # double maxima and dt: the same operations
+    else:
+        assert torch.allclose(da, db, rtol=1e-6, atol=0)   # float speeds, contracted per kernel
+    dt = 0.1 * min(1.0 / n for sh in SHAPES for n in sh)
+    a.step(dt)
+    b.step(dt)
+    a.step_dev(da)
+    b.step_dev(db)
+    a.step_graph(2)
+    b.step_graph(2)
+    a.synchronize()
+    b.synchronize()
+    tol = 1e-13 if precision == 0 else 1e-5
+    for p in range(len(SHAPES)):
+        for x, y in zip(a.get_state(p), b.get_state(p)):
+            assert np.abs(x - y).max() <= tol * np.abs(x).max(), ("patch", p)
+    assert b.status() == a.status()
+    a.close()
+    b.close()
+
+
+def test_fused_step_many_small_patches(env):
+    """Many patches smaller than one tile: most items of a stage wait on
+    others of their patch (the dependency chains of the work queue)."""
+    shapes = [(8 + (p % 3) * 4, 6 + (p % 2) * 5, 4 + (p % 4)) for p in range(40)]
+    sts = [env["I"].random_smooth_state(sh, seed=1200 + p) for p, sh in enumerate(shapes)]
+    a = make_batch(env, shapes, sts, 0, 1)
+    b = make_batch(env, shapes, sts, 0, 1)
+    b.set_schedule(2)
+    for _ in range(3):
+        a.step_cfl()
+        b.step_cfl()
+    a.synchronize()
+    b.synchronize()
+    for p in range(len(shapes)):
+        for x, y in zip(a.get_state(p), b.get_state(p)):
+            assert np.abs(x - y).max() <= 1e-13 * np.abs(x).max(), ("patch", p)
+    a.close()
+    b.close()
