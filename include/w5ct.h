@@ -168,11 +168,11 @@ int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
  * device at once, each block taking tiles of all three axes from a device
  * work queue (an atomically incremented counter, zeroed at the start of every
  * step) until the list is exhausted; no block waits on another.  2: the
- * whole step (cell fields, CFL reduction and dt, the sweeps in 32-lane tiles,
- * the four stage updates) in one persistent launch over a work queue in
- * which each item waits, with bounded spins, for the earlier items of its own
- * patch that it depends on; an expired wait aborts the launch and the next
- * synchronising call returns W5CT_ERR_TIMEOUT.  Every face and cell is
+ * whole step (cell fields, CFL reduction and dt, the sweeps in 32- or
+ * 16-lane tiles, the four stage updates) in one persistent launch over a
+ * work queue in which each item waits, with bounded spins, for the earlier
+ * items of its own patch that it depends on; an expired wait aborts the
+ * launch and the next synchronising call returns W5CT_ERR_TIMEOUT.  Every face and cell is
  * computed from the same source in all schedules; the compiler may contract a
  * few operations differently in the fused kernels, so the results agree to
  * rounding (not bit for bit).  w5ct_autotune(W5CT_TUNE_MEASURE) times whole
@@ -181,6 +181,15 @@ int w5ct_autotune(w5ct_ctx *ctx, int mode, int reps);
  * patch. */
 int w5ct_set_sweep_schedule(w5ct_ctx *ctx, int schedule);
 int w5ct_sweep_schedule(w5ct_ctx *ctx, int *schedule);
+
+/* Check of the fused step's failure path (npatch > 1, state set; any
+ * schedule): launches the fused kernel on a one-item work list whose
+ * dependency nothing satisfies, each wait bounded by spin_limit sleeps of
+ * 256 ns (1 <= spin_limit <= 2^22).  The wait expires, the launch aborts and
+ * ends, and *status receives what a synchronising call then reports
+ * (W5CT_ERR_TIMEOUT when the bound works).  The state is not touched and the
+ * context's flag is restored afterwards.  Synchronises the stream. */
+int w5ct_fused_wait_check(w5ct_ctx *ctx, long long spin_limit, int *status);
 
 /* out[3] = {variant, BX, T2} of the tiles that sweep patch `patch` along
  * `axis` (0, 1, 2).  Host only. */

@@ -25,11 +25,8 @@ CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # reciprocal / square root and flushes subnormals; every double operation
 # and every other translation unit stays IEEE.
 FAST_FLOAT = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-# The fused step kernel reads data that other blocks of the same launch
-# wrote: its global loads bypass L1 (-dlcm=cg).
-L2_ONLY = ["-Xptxas", "-dlcm=cg"]
 TU_FLAGS = {"w5ct_sweep32.cu": FAST_FLOAT, "w5ct_adjoint32z.cu": FAST_FLOAT, "w5ct_adjoint32js.cu": FAST_FLOAT,
-            "w5ct_fused32.cu": FAST_FLOAT + L2_ONLY, "w5ct_fused64.cu": L2_ONLY}
+            "w5ct_fused32.cu": FAST_FLOAT}
 
 
 def _newest_input() -> float:

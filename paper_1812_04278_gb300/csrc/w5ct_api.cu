@@ -67,6 +67,7 @@ struct w5ct_ctx {
     int4 *fused_items = nullptr;
     int nfused = 0;
     int *fused_ncb = nullptr, *fused_ntile = nullptr, *fused_done = nullptr, *fused_qa = nullptr;
+    int4 *fused_check = nullptr;     // one-item list of w5ct_fused_wait_check
     int fused_blocks = 0;
     int pgrid[kMaxTileVariants] = {};   // resident blocks of the persistent sweep per variant
     int *pcounters = nullptr;        // work-queue counters: 4 stages x kMaxTileVariants
@@ -244,10 +245,16 @@ int build_tiles(w5ct_ctx *c) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
+    if (c->tiles_buf || c->fused_buf) W5_CUDA(c, cudaStreamSynchronize(c->stream));
     if (c->tiles_buf) {
-        W5_CUDA(c, cudaStreamSynchronize(c->stream));
         cudaFree(c->tiles_buf);
         c->tiles_buf = nullptr;
+    }
+    // the fused step's work list follows the variants: rebuilt on next use
+    if (c->fused_buf) {
+        cudaFree(c->fused_buf);
+        c->fused_buf = nullptr;
+        c->nfused = 0;
     }
     W5_CUDA(c, cudaMalloc(&c->tiles_buf, sizeof(int4) * all.size()));
     W5_CUDA(c, cudaMemcpy(c->tiles_buf, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice));
@@ -371,47 +378,59 @@ int build_fused(w5ct_ctx *c) {
     std::vector<int4> items;
     std::vector<int> ncb(c->npatch), ntile(c->npatch, 0);
     const bool fp64 = c->cfg.precision == W5CT_FP64;
-    const int t2x = fp64 ? sweep_t2<double>(0) : sweep_t2<float>(0);
-    const int t2yz = fp64 ? sweep_t2<double>(1) : sweep_t2<float>(1);
     for (int p = 0; p < c->npatch; ++p) {
         const PatchGeom &g = c->pg[p];
-        ncb[p] = (int)(((long long)g.nx * g.ny * g.nz + 255) / 256);
+        ncb[p] = (int)(((long long)g.nx * g.ny * g.nz + kFusedCells - 1) / kFusedCells);
     }
     // Phase-major within a stage (every patch's cell fields, then CFL blocks
     // and dts, then sweeps, then updates): an item's dependencies then lie a
     // whole phase back in the queue and are usually done when it is taken.
     for (int st = 0; st < 4; ++st) {
         for (int p = 0; p < c->npatch; ++p)
-            for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_CELLB, st, 0, 0), q * 256, 0));
+            for (int q = 0; q < ncb[p]; ++q)
+                items.push_back(make_int4(p, fused_tag(FI_CELLB, st, 0, 0), q * kFusedCells, 0));
         if (st == 0) {
             for (int p = 0; p < c->npatch; ++p)
-                for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_SPEED, 0, 0, 0), q * 256, 0));
+                for (int q = 0; q < ncb[p]; ++q)
+                    items.push_back(make_int4(p, fused_tag(FI_SPEED, 0, 0, 0), q * kFusedCells, 0));
             for (int p = 0; p < c->npatch; ++p) items.push_back(make_int4(p, fused_tag(FI_DT, 0, 0, 0), 0, 0));
         }
+        // per patch and axis: the tiles of the patch's tile variant, one per
+        // item; the fused kernel has the two 256-thread variants (0 and 1),
+        // a patch tuned to a narrower one takes the better of the two by
+        // the tile cost model
         for (int p = 0; p < c->npatch; ++p) {
             const PatchGeom &g = c->pg[p];
             const size_t before = items.size();
-            const int nbx = (g.nx + 31) / 32;
-            for (int k = 0; k < g.nz; ++k)
-                for (int j = 0; j < (g.ny + t2x - 1) / t2x; ++j)
-                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 0, i), j, k));
-            for (int k = 0; k < g.nz; ++k)
-                for (int j = 0; j < (g.ny + t2yz - 1) / t2yz; ++j)
-                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 1, i), j, k));
-            for (int k = 0; k < (g.nz + t2yz - 1) / t2yz; ++k)
-                for (int j = 0; j < g.ny; ++j)
-                    for (int i = 0; i < nbx; ++i) items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, 2, i), j, k));
+            for (int a = 0; a < 3; ++a) {
+                int v = c->pvar[a][p];
+                if (v > 1) {
+                    int b0, h0, b1, h1;
+                    variant_shape(c, a, 0, b0, h0);
+                    variant_shape(c, a, 1, b1, h1);
+                    v = tile_model_cost(g, a, b1, h1) < tile_model_cost(g, a, b0, h0) ? 1 : 0;
+                }
+                int bx, t2;
+                variant_shape(c, a, v, bx, t2);
+                const long long nbx = (g.nx + bx - 1) / bx;
+                const long long nb1 = a == 2 ? g.ny : (g.ny + t2 - 1) / t2;
+                const long long nb2 = a == 2 ? (g.nz + t2 - 1) / t2 : g.nz;
+                const long long ntiles = nbx * nb1 * nb2;
+                for (long long L = 0; L < ntiles; ++L)
+                    items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, a, v), (int)L, 0));
+            }
             if (st == 0) ntile[p] = (int)(items.size() - before);
         }
         for (int p = 0; p < c->npatch; ++p)
-            for (int q = 0; q < ncb[p]; ++q) items.push_back(make_int4(p, fused_tag(FI_UPDATE, st, 0, 0), q * 256, 0));
+            for (int q = 0; q < ncb[p]; ++q)
+                items.push_back(make_int4(p, fused_tag(FI_UPDATE, st, 0, 0), q * kFusedCells, 0));
     }
     if (items.size() > (size_t)0x7fffffff) return fail(c, W5CT_ERR_ARG, "too many work items for the fused step");
     const size_t P = (size_t)c->npatch;
     size_t bytes = 0;
     auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
     const size_t o_it = take(sizeof(int4) * items.size()), o_ncb = take(sizeof(int) * P), o_nt = take(sizeof(int) * P);
-    const size_t o_done = take(sizeof(int) * 14 * P), o_qa = take(sizeof(int) * 2);
+    const size_t o_done = take(sizeof(int) * 14 * P), o_qa = take(sizeof(int) * 2), o_chk = take(sizeof(int4));
     W5_CUDA(c, cudaMalloc(&c->fused_buf, bytes));
     char *b = (char *)c->fused_buf;
     c->fused_items = (int4 *)(b + o_it);
@@ -419,7 +438,12 @@ int build_fused(w5ct_ctx *c) {
     c->fused_ntile = (int *)(b + o_nt);
     c->fused_done = (int *)(b + o_done);
     c->fused_qa = (int *)(b + o_qa);
+    c->fused_check = (int4 *)(b + o_chk);
     c->nfused = (int)items.size();
+    // the failure-path check's list: patch 0's first stage-0 update alone
+    // (its sweep counter is never raised)
+    const int4 chk = make_int4(0, fused_tag(FI_UPDATE, 0, 0, 0), 0, 0);
+    W5_CUDA(c, cudaMemcpy(c->fused_check, &chk, sizeof(int4), cudaMemcpyHostToDevice));
     W5_CUDA(c, cudaMemcpy(c->fused_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     W5_CUDA(c, cudaMemcpy(c->fused_ncb, ncb.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
     W5_CUDA(c, cudaMemcpy(c->fused_ntile, ntile.data(), sizeof(int) * P, cudaMemcpyHostToDevice));
@@ -430,11 +454,16 @@ int build_fused(w5ct_ctx *c) {
     return W5CT_OK;
 }
 
+// Bound of a fused-step wait: 2^22 sleeps of 256 ns, about a second.
+constexpr long long kFusedSpinLimit = 1LL << 22;
+
 // One step of every patch in one persistent launch: dts given (device,
 // npatch doubles) or, when dts_in is NULL, from each patch's CFL condition
-// (copied to dts_out when not NULL).
+// (copied to dts_out when not NULL).  `check`: run the one-item list of the
+// failure-path check instead, waits bounded by spin_limit.
 template <typename Real>
-int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out) {
+int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out, bool check = false,
+                    long long spin_limit = kFusedSpinLimit) {
     int rc = build_fused(c);
     if (rc) return rc;
     const long long n = c->n;
@@ -465,8 +494,8 @@ int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out) {
         A.bc[f] = plane<Real>(c->bc, n, f);
     }
     A.pgs = c->pg_dev;
-    A.items = c->fused_items;
-    A.nitems = c->nfused;
+    A.items = check ? c->fused_check : c->fused_items;
+    A.nitems = check ? 1 : c->nfused;
     A.ncb = c->fused_ncb;
     A.ntile = c->fused_ntile;
     A.ctr.queue = c->fused_qa;
@@ -478,7 +507,7 @@ int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out) {
     A.dts = dts_in ? const_cast<double *>(dts_in) : c->dt_dev;
     A.dts_out = dts_in ? nullptr : dts_out;
     A.smax = c->smax;
-    A.spin_limit = 1LL << 22;   // x 256 ns of sleep: about a second
+    A.spin_limit = spin_limit;
     int e0 = record_event(c);
     if (e0) return e0;
     W5_CUDA(c, launch_fused_step<Real>(c->cfg.weno_variant, A, c->fused_blocks, st));
@@ -1322,6 +1351,29 @@ int w5ct_set_sweep_schedule(w5ct_ctx *c, int schedule) {
         c->gexec = nullptr;
     }
     c->schedule = schedule;
+    return W5CT_OK;
+}
+
+int w5ct_fused_wait_check(w5ct_ctx *c, long long spin_limit, int *status) {
+    if (!c || !status) return W5CT_ERR_ARG;
+    if (!c->have_grid || !c->have_state) return fail(c, W5CT_ERR_STATE, "call w5ct_init_grid and set the state first");
+    if (c->npatch == 1) return fail(c, W5CT_ERR_UNSUPPORTED, "the fused step takes a batch of patches");
+    if (spin_limit < 1 || spin_limit > kFusedSpinLimit)
+        return fail(c, W5CT_ERR_ARG, "spin_limit must be in [1, 2^22]");
+    int rc = build_fused(c);
+    if (rc) return rc;
+    int flag0 = 0;
+    rc = read_flag(c, &flag0);
+    if (rc) return rc;
+    rc = c->cfg.precision == W5CT_FP64 ? fused_step_impl<double>(c, nullptr, nullptr, true, spin_limit)
+                                       : fused_step_impl<float>(c, nullptr, nullptr, true, spin_limit);
+    if (rc) return rc;
+    int flag = 0;
+    rc = read_flag(c, &flag);
+    if (rc) return rc;
+    *status = (flag & 2) ? W5CT_ERR_TIMEOUT : (flag ? W5CT_ERR_NONPHYSICAL : W5CT_OK);
+    W5_CUDA(c, cudaMemcpyAsync(c->flag, &flag0, sizeof(flag0), cudaMemcpyHostToDevice, c->stream));
+    W5_CUDA(c, cudaStreamSynchronize(c->stream));
     return W5CT_OK;
 }
 

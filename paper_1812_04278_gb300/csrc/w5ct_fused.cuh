@@ -2,10 +2,12 @@
 // persistent launch (the fused schedule of the batched path).
 //
 // The step is a list of work items, built on the host: per stage s and patch
-// p, the 256-cell blocks of p's cell field (Sec. 2.3), at s = 0 the blocks of
-// p's CFL reduction (Eq. cfl) and p's dt, the sweep tiles of p along x, y and
-// z (Sec. 2.2), and the blocks of p's stage update (Eq. num, Sec. 2.1, Eqs.
-// ox1-ox3).  Each block of the persistent grid takes the next item from a
+// p, the blocks of kFusedCells cells of p's cell field (Sec. 2.3), at s = 0
+// the blocks of p's CFL reduction (Eq. cfl) and p's dt, the sweep tiles of p
+// along x, y and z (Sec. 2.2), and the blocks of p's stage update (Eq. num,
+// Sec. 2.1, Eqs. ox1-ox3), ordered phase by phase within a stage (every
+// patch's cell fields, then the CFL items, then the sweeps, then the
+// updates).  Each block of the persistent grid takes the next item from a
 // device counter and first waits until the items it depends on -- all of
 // them earlier in the list and all of the same patch -- are done:
 //
@@ -18,17 +20,20 @@
 // A dependency is always dequeued before the item that waits on it, by a
 // block that is running, and waits only point backwards in the list, so the
 // chain of waits ends at an item that can finish: the launch completes
-// without any assumption on how many blocks are resident.  Every wait is
+// without any assumption on how many blocks are resident.  A block fetches
+// its next item index while it works on the current one, and skips the
+// check of a dependency it has already seen complete (counters only grow
+// within a step).  Every wait is
 // bounded (an iteration limit with a short sleep): on expiry the block sets
 // bit 2 of the context's flag and an abort word that makes every other block
 // stop, and the step reports W5CT_ERR_TIMEOUT.
 //
 // Memory ordering: a block publishes an item with __syncthreads, a fence and
-// an atomicAdd on the item's counter; a waiter spins on the counter, fences,
-// and releases its threads with __syncthreads (the grid-synchronisation
-// pattern).  The translation units of this kernel are compiled with global
-// loads cached in L2 only (-dlcm=cg), so no block reads a line left in its
-// SM's L1 by an earlier item.
+// an atomicAdd on the item's counter (a release pattern of the PTX memory
+// model); a waiter reads the counter, fences (an acquire pattern) and
+// releases its threads with __syncthreads, which orders their loads after
+// the producer's stores (the grid-synchronisation pattern).  No load of the
+// kernel goes through the non-coherent read-only path.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -38,11 +43,28 @@ namespace w5ct {
 
 enum FusedItem { FI_CELLB = 0, FI_SPEED = 1, FI_DT = 2, FI_SWEEP = 3, FI_UPDATE = 4 };
 
-// item: x = patch, y = type | stage << 3 | axis << 5 | tbx << 8, z, w =
-// (tby, tbz) of a sweep tile or (first cell, 0) of a cell block
-__host__ __device__ inline int fused_tag(int type, int stage, int axis, int tbx) {
-    return type | (stage << 3) | (axis << 5) | (tbx << 8);
+// cells of one cell-wise item (four per thread of a 256-thread block): the
+// per-item bookkeeping (queue, dependency check, fence, counter) is then
+// shared by 1024 cells
+constexpr int kFusedCells = 1024;
+
+// item: x = patch, y = type | stage << 3 | axis << 5 | v << 8; for a sweep
+// item z = tile index i + nbx (j + nb1 k) among the patch's tiles of variant
+// v along the axis (the order of the tile tables), for a cell-wise item z =
+// its first cell; w = 0
+__host__ __device__ inline int fused_tag(int type, int stage, int axis, int v) {
+    return type | (stage << 3) | (axis << 5) | (v << 8);
 }
+
+// Tile variant V (0 or 1: 256 threads, the fused kernel's block) of the
+// sweep along AX and its shared memory.
+template <typename Real, int AX, int V>
+struct FusedTile {
+    using C = TileV<AX, Real, V>;
+    using TT = SweepTile<AX, C::T2, C::BX, C::FPT>;
+    static_assert(TT::NT == 256, "one tile per 256-thread block");
+    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+};
 
 // Per-patch completion counters, zeroed at the start of every step:
 // cellb[s][p], sweep[s][p], update[s][p], speed[p], dt[p].
@@ -67,7 +89,7 @@ struct FusedArgs {
     const PatchGeom *pgs;
     const int4 *items;
     int nitems;
-    const int *ncb;              // cell blocks per patch
+    const int *ncb;              // cell-wise items per patch
     const int *ntile;            // sweep tiles (three axes) per patch
     FusedCounters ctr;
     int cfl;                     // 1: dt of each patch from its state; 0: dts given
@@ -78,14 +100,18 @@ struct FusedArgs {
     long long spin_limit;
 };
 
-// thread 0 of a block: wait until *ctr >= target; false if aborted or expired
+// thread 0 of a block: wait until *ctr >= target; false if aborted or
+// expired.  seen[0..1]: the last two counters this block saw complete.
 __device__ __forceinline__ bool fused_wait(const FusedCounters &C, const int *ctr, int target, long long limit,
-                                           int *flag) {
+                                           int *flag, const int *(&seen)[2]) {
+    if (ctr == seen[0] || ctr == seen[1]) return true;
     long long it = 0;
     for (;;) {
         const int v = *(volatile const int *)ctr;
         if (v >= target) {
             __threadfence();
+            seen[1] = seen[0];
+            seen[0] = ctr;
             return true;
         }
         if (*(volatile const int *)C.abort) return false;
@@ -115,6 +141,21 @@ __device__ __forceinline__ void fused_cellb(const PatchGeom &g, int i, int j, in
     Bz[p] = (Real(9) * (bz[p + zm1] + bz[p]) - (bz[p + zm2] + bz[p + zp1])) * s;
 }
 
+// Tile L of variant V (0 or 1: one tile of 256 threads per block) of a
+// patch along AX.
+template <int AX, typename Real, int VAR, int V>
+__device__ __forceinline__ void fused_sweep(const SweepArgs<Real> &a, const PatchGeom &pg, int L, int tid, Real *sm) {
+    using Cv = typename FusedTile<Real, AX, V>::C;
+    const int nbx = (pg.nx + Cv::BX - 1) / Cv::BX;
+    const int nb1 = AX == 2 ? pg.ny : (pg.ny + Cv::T2 - 1) / Cv::T2;
+    const int r = L / nbx;
+    const int i = L - r * nbx, k = r / nb1, j = r - k * nb1;
+    // blockDim = (32, 8): variant 0 uses the block's own thread indices
+    const int tx = Cv::BX == 32 ? (int)threadIdx.x : tid % Cv::BX;
+    const int ty = Cv::BX == 32 ? (int)threadIdx.y : tid / Cv::BX;
+    sweep_tile_at<AX, Real, VAR, Cv::T2, Cv::BX, Cv::FPT>(a, pg, i, j, k, sm, tx, ty);
+}
+
 template <typename Real, int VAR>
 __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kernel(FusedArgs<Real> A) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
@@ -123,28 +164,35 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
     Real *sm = reinterpret_cast<Real *>(w5ct_smem);
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const FusedCounters &C = A.ctr;
+    const int *seen[2] = {nullptr, nullptr};    // thread 0: counters seen complete
+    int next = 0;
+    if (tid == 0) next = atomicAdd(C.queue, 1);
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(C.queue, 1);
+        if (tid == 0) s_item = next;
         __syncthreads();
         const int it = s_item;
         if (it >= A.nitems) break;
+        // the following item, fetched while this one runs
+        if (tid == 0) next = atomicAdd(C.queue, 1);
         const int4 t = A.items[it];
         const int p = t.x;
-        const int type = t.y & 7, stage = (t.y >> 3) & 3, axis = (t.y >> 5) & 3, tbx = t.y >> 8;
+        const int type = t.y & 7, stage = (t.y >> 3) & 3, axis = (t.y >> 5) & 3, v = t.y >> 8;
         const PatchGeom pg = A.pgs[p];
         // ---- wait for this item's dependencies (thread 0), then release the block
         if (tid == 0) {
             bool ok = true;
             switch (type) {
                 case FI_CELLB:
-                    if (stage > 0) ok = fused_wait(C, C.update(stage - 1, p), A.ncb[p], A.spin_limit, A.a[0].flag);
+                    if (stage > 0) ok = fused_wait(C, C.update(stage - 1, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen);
                     break;
-                case FI_SPEED: ok = fused_wait(C, C.cellb(0, p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
-                case FI_DT: ok = fused_wait(C, C.speed(p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
-                case FI_SWEEP: ok = fused_wait(C, C.cellb(stage, p), A.ncb[p], A.spin_limit, A.a[0].flag); break;
+                case FI_SPEED: ok = fused_wait(C, C.cellb(0, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen); break;
+                case FI_DT: ok = fused_wait(C, C.speed(p), A.ncb[p], A.spin_limit, A.a[0].flag, seen); break;
+                case FI_SWEEP:
+                    ok = fused_wait(C, C.cellb(stage, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen);
+                    break;
                 default:
-                    ok = fused_wait(C, C.sweep(stage, p), A.ntile[p], A.spin_limit, A.a[0].flag);
-                    if (ok && stage == 0) ok = fused_wait(C, C.dtc(p), 1, A.spin_limit, A.a[0].flag);
+                    ok = fused_wait(C, C.sweep(stage, p), A.ntile[p], A.spin_limit, A.a[0].flag, seen);
+                    if (ok && stage == 0) ok = fused_wait(C, C.dtc(p), 1, A.spin_limit, A.a[0].flag, seen);
                     break;
             }
             s_ok = ok ? 1 : 0;
@@ -154,12 +202,24 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
         // ---- the item's work
         int *done = nullptr;
         if (type == FI_SWEEP) {
-            if (axis == 0)
-                sweep_tile<0, Real, VAR, SweepTuning<Real>::T2X>(A.a[0], pg, tbx, t.z, t.w, sm);
-            else if (axis == 1)
-                sweep_tile<1, Real, VAR, SweepTuning<Real>::T2YZ>(A.a[1], pg, tbx, t.z, t.w, sm);
-            else
-                sweep_tile<2, Real, VAR, SweepTuning<Real>::T2YZ>(A.a[2], pg, tbx, t.z, t.w, sm);
+            if constexpr (sizeof(Real) == 4) {
+                switch (axis * 2 + v) {
+                    case 0: fused_sweep<0, Real, VAR, 0>(A.a[0], pg, t.z, tid, sm); break;
+                    case 1: fused_sweep<0, Real, VAR, 1>(A.a[0], pg, t.z, tid, sm); break;
+                    case 2: fused_sweep<1, Real, VAR, 0>(A.a[1], pg, t.z, tid, sm); break;
+                    case 3: fused_sweep<1, Real, VAR, 1>(A.a[1], pg, t.z, tid, sm); break;
+                    case 4: fused_sweep<2, Real, VAR, 0>(A.a[2], pg, t.z, tid, sm); break;
+                    default: fused_sweep<2, Real, VAR, 1>(A.a[2], pg, t.z, tid, sm); break;
+                }
+            } else {
+                // the FP64 sweeps have one tile shape
+                if (axis == 0)
+                    fused_sweep<0, Real, VAR, 0>(A.a[0], pg, t.z, tid, sm);
+                else if (axis == 1)
+                    fused_sweep<1, Real, VAR, 0>(A.a[1], pg, t.z, tid, sm);
+                else
+                    fused_sweep<2, Real, VAR, 0>(A.a[2], pg, t.z, tid, sm);
+            }
             done = C.sweep(stage, p);
         } else if (type == FI_DT) {
             if (tid == 0 && A.cfl) {
@@ -173,23 +233,33 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
             }
             done = C.dtc(p);
         } else {
-            // a block of 256 consecutive cells of the patch
-            const int idx = t.z + tid;
-            const bool in = idx < pg.nx * pg.ny * pg.nz;
-            const int row = idx / pg.nx;
-            const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
+            // kFusedCells consecutive cells of the patch (storage order),
+            // cells t.z + tid + 256 r
+            const int ncell = pg.nx * pg.ny * pg.nz;
             if (type == FI_CELLB) {
-                if (in) fused_cellb<Real>(pg, i, j, k, A.bs[0], A.bs[1], A.bs[2], A.bc[0], A.bc[1], A.bc[2]);
+#pragma unroll 1
+                for (int r = 0; r < kFusedCells / 256; ++r) {
+                    const int idx = t.z + tid + 256 * r;
+                    if (idx < ncell) {
+                        const int row = idx / pg.nx;
+                        const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
+                        fused_cellb<Real>(pg, i, j, k, A.bs[0], A.bs[1], A.bs[2], A.bc[0], A.bc[1], A.bc[2]);
+                    }
+                }
                 done = C.cellb(stage, p);
             } else if (type == FI_SPEED) {
                 if (A.cfl) {
                     double v[3] = {0.0, 0.0, 0.0};
                     bool bad = false;
-                    if (in) {
-                        const size_t q = (size_t)pg.off + (size_t)idx;
-                        const SweepArgs<Real> &a = A.a[0];
-                        cell_speeds<Real>(a.q[0][q], a.q[1][q], a.q[2][q], a.q[3][q], a.q[4][q], a.bc[0][q],
-                                          a.bc[1][q], a.bc[2][q], a.K, v, bad);
+#pragma unroll 1
+                    for (int r = 0; r < kFusedCells / 256; ++r) {
+                        const int idx = t.z + tid + 256 * r;
+                        if (idx < ncell) {
+                            const size_t q = (size_t)pg.off + (size_t)idx;
+                            const SweepArgs<Real> &a = A.a[0];
+                            cell_speeds<Real>(a.q[0][q], a.q[1][q], a.q[2][q], a.q[3][q], a.q[4][q], a.bc[0][q],
+                                              a.bc[1][q], a.bc[2][q], a.K, v, bad);
+                        }
                     }
                     if (bad) atomicOr(A.a[0].flag, 1);
                     // maxima over the block's eight warps
@@ -211,10 +281,15 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
                 }
                 done = C.speed(p);
             } else {
-                if (in) {
-                    const UpdGeom<Real> ug = {pg.nx, pg.ny, pg.nz, (size_t)pg.off, (Real)pg.rdx, (Real)pg.rdy,
-                                              (Real)pg.rdz, pg.rdx, pg.rdy, pg.rdz};
-                    const double dt = A.dts[p];
+                const UpdGeom<Real> ug = {pg.nx, pg.ny, pg.nz, (size_t)pg.off, (Real)pg.rdx, (Real)pg.rdy,
+                                          (Real)pg.rdz, pg.rdx, pg.rdy, pg.rdz};
+                const double dt = A.dts[p];
+#pragma unroll 1
+                for (int r = 0; r < kFusedCells / 256; ++r) {
+                    const int idx = t.z + tid + 256 * r;
+                    if (idx >= ncell) break;
+                    const int row = idx / pg.nx;
+                    const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
                     switch (stage) {
                         case 0: update_cell<Real, 0>(A.u, ug, i, j, k, dt); break;
                         case 1: update_cell<Real, 1>(A.u, ug, i, j, k, dt); break;
@@ -240,15 +315,19 @@ cudaError_t launch_fused_step(int variant, const FusedArgs<Real> &A, int blocks,
 template <typename Real>
 cudaError_t fused_grid(int variant, int &blocks, size_t &smem);
 
+template <typename Real, int V>
+constexpr size_t fused_smem_v() {
+    constexpr size_t a = FusedTile<Real, 0, V>::smem, b = FusedTile<Real, 1, V>::smem, c = FusedTile<Real, 2, V>::smem;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+// shared memory of the fused kernel: the largest item (variants 0..3 in
+// float, 0 in double)
 template <typename Real, int VAR>
 size_t fused_smem() {
-    using T0 = SweepTile<0, SweepTuning<Real>::T2X>;
-    using T1 = SweepTile<1, SweepTuning<Real>::T2YZ>;
-    using T2_ = SweepTile<2, SweepTuning<Real>::T2YZ>;
-    size_t m = (size_t)T0::NC;
-    if ((size_t)T1::NC > m) m = (size_t)T1::NC;
-    if ((size_t)T2_::NC > m) m = (size_t)T2_::NC;
-    return m * NCQ * sizeof(Real);
+    size_t m = fused_smem_v<Real, 0>();
+    if (sizeof(Real) == 4 && fused_smem_v<Real, 1>() > m) m = fused_smem_v<Real, 1>();
+    return m;
 }
 
 template <typename Real, int VAR>

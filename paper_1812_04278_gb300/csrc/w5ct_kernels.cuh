@@ -71,17 +71,18 @@ struct PatchGeom {
     double dx, dy, dz;
 };
 
-// One sweep tile (tile indices tbx, tby, tbz) of the patch described by g.
-// sm: dynamic shared memory of NCQ * NC elements.
-template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8>
-__device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
-                                           Real *sm) {
+// One sweep tile (tile indices tbx, tby, tbz) of the patch described by g,
+// computed by the block's NT threads, numbered (tx, ty) in [0, BX) x
+// [0, ROWS).  sm: shared memory of NCQ * NC elements.
+template <int AX, typename Real, int VAR, int T2, int BX, int FPT>
+__device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
+                                              Real *sm, int tx, int ty) {
     using TT = SweepTile<AX, T2, BX, FPT>;
     const int nx = pg.nx, ny = pg.ny, nz = pg.nz;
     const size_t off = (size_t)pg.off;
     const int x0 = tbx * TT::BX, y0 = tby * TT::BY, z0 = tbz * TT::BZ;
     const int ox = x0 - (AX == 0 ? 2 : 0), oy = y0 - (AX == 1 ? 2 : 0), oz = z0 - (AX == 2 ? 2 : 0);
-    const int tid = threadIdx.x + TT::BX * threadIdx.y;
+    const int tid = tx + TT::BX * ty;
 
     // phase 1: per-cell primitives, flux and speeds of the cell box
     bool bad = false, hit = false;
@@ -104,8 +105,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const Patch
     // phase 2: FPT interfaces per thread
 #pragma unroll 1
     for (int r = 0; r < TT::FPT; ++r) {
-        const int t2 = threadIdx.y + TT::ROWS * r;
-        const int bx = threadIdx.x;
+        const int t2 = ty + TT::ROWS * r;
+        const int bx = tx;
         const int by = (AX == 2) ? 0 : t2;
         const int bz = (AX == 2) ? t2 : 0;
         const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
@@ -123,6 +124,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const Patch
             a.S[1][g] = s2;
         }
     }
+}
+
+// One tile computed by the whole block, blockDim = (BX, ROWS).
+template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8>
+__device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
+                                           Real *sm) {
+    sweep_tile_at<AX, Real, VAR, T2, BX, FPT>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
 }
 
 template <int AX, typename Real, int VAR, int T2, int MINB>

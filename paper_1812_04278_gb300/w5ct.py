@@ -44,6 +44,7 @@ EXPORTED = [
     "w5ct_launch_count", "w5ct_last_error", "w5ct_conserved_totals_noalloc", "w5ct_step_graph",
     "w5ct_autotune", "w5ct_tile_variant", "w5ct_adjoint_step", "w5ct_misfit", "w5ct_ic_from_potential",
     "w5ct_ic_from_potential_adjoint", "w5ct_set_sweep_schedule", "w5ct_sweep_schedule",
+    "w5ct_fused_wait_check",
 ]
 W5CT_TUNE_MEASURE = -1
 W5CT_TUNE_MODEL = -2
@@ -75,6 +76,7 @@ _sig = {
     "w5ct_adjoint_step": [_VP, c_double, _VP, _VP, _VP, _VP],
     "w5ct_set_sweep_schedule": [_VP, c_int],
     "w5ct_sweep_schedule": [_VP, POINTER(c_int)],
+    "w5ct_fused_wait_check": [_VP, c_longlong, POINTER(c_int)],
     "w5ct_misfit": [_VP, _VP, _VP, _DP, _VP, _VP],
     "w5ct_ic_from_potential": [POINTER(c_int), _DP, c_double, _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "w5ct_ic_from_potential_adjoint": [POINTER(c_int), _DP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
@@ -199,6 +201,14 @@ def w5ct_set_sweep_schedule(ctx, schedule: int):
 def w5ct_sweep_schedule(ctx) -> int:
     out = c_int()
     _check(_lib.w5ct_sweep_schedule(ctx, ctypes.byref(out)), "w5ct_sweep_schedule", ctx)
+    return out.value
+
+
+def w5ct_fused_wait_check(ctx, spin_limit: int) -> int:
+    """Status a synchronising call reports after a fused-step wait bounded by
+    spin_limit sleeps expires (W5CT_ERR_TIMEOUT when the bound works)."""
+    out = c_int()
+    _check(_lib.w5ct_fused_wait_check(ctx, int(spin_limit), ctypes.byref(out)), "w5ct_fused_wait_check", ctx)
     return out.value
 
 

@@ -328,3 +328,40 @@ def test_fused_step_many_small_patches(env):
             assert np.abs(x - y).max() <= 1e-13 * np.abs(x).max(), ("patch", p)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_wait_expiry_reports_timeout(env, precision):
+    """A fused-step wait that nothing satisfies (a one-item work list whose
+    sweep dependency is never done) ends after its bound: the launch aborts
+    and ends on its own, the status reads W5CT_ERR_TIMEOUT, the state is
+    untouched, and the context then steps like a fresh one."""
+    import time
+    W = env["W"]
+    sts = states(env, SHAPES, 1300 + precision)
+    a = make_batch(env, SHAPES, sts, precision, 1)
+    b = make_batch(env, SHAPES, sts, precision, 1)
+    before = [b.get_state(p) for p in range(len(SHAPES))]
+    t0 = time.perf_counter()
+    status = W.w5ct_fused_wait_check(b.ctx, 1000)       # 1000 sleeps of 256 ns
+    elapsed = time.perf_counter() - t0
+    assert status == W.W5CT_ERR_TIMEOUT
+    assert elapsed < 5.0
+    for p in range(len(SHAPES)):
+        for x, y in zip(before[p], b.get_state(p)):
+            assert np.array_equal(x, y), ("state changed by the aborted launch", p)
+    assert b.status()[1] == 0                           # flag restored
+    b.set_schedule(2)
+    for _ in range(2):
+        a.step_cfl()
+        b.step_cfl()
+    a.synchronize()
+    b.synchronize()
+    tol = 1e-13 if precision == 0 else 1e-5
+    for p in range(len(SHAPES)):
+        for x, y in zip(a.get_state(p), b.get_state(p)):
+            assert np.abs(x - y).max() <= tol * np.abs(x).max(), ("patch", p)
+    with pytest.raises(Exception):
+        W.w5ct_fused_wait_check(b.ctx, 0)                # bound out of range
+    a.close()
+    b.close()
