@@ -269,6 +269,49 @@ struct UpdGeom {
     double drdx, drdy, drdz;     // 1/dx etc. (final FP64 curl)
 };
 
+// float <-> double conversions done on the integer pipes for finite normal
+// values, from the IEEE 754 binary32 / binary64 layouts (exponent bias 127 /
+// 1023, 23 / 52 fraction bits); double -> float rounds to nearest, ties to
+// even, so both equal the hardware conversions bit for bit.  Zeros,
+// subnormals, infinities and NaNs take the hardware conversion.  A
+// conversion that involves double issues to the FP64 pipe, which the
+// FP32-bulk stage update keeps busy with its accumulations.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int fe = (int)((u >> 52) & 0x7ffu) - 896;          // binary32 exponent field
+    if (fe < 1 || fe > 254) return (float)x;
+    const unsigned long long m = u & 0xfffffffffffffULL;
+    const unsigned mant = (unsigned)(m >> 29);
+    const unsigned long long rem = m & 0x1fffffffULL, half = 1ULL << 28;
+    unsigned r = ((unsigned)(u >> 32) & 0x80000000u) | ((unsigned)fe << 23) | mant;
+    if (rem > half || (rem == half && (mant & 1u))) ++r;     // a carry moves into the exponent (or to inf)
+    return __uint_as_float(r);
+}
+
+template <typename Real>
+__device__ __forceinline__ double to_double(Real x) {
+    if constexpr (std::is_same<Real, float>::value)
+        return f2d_exact(x);
+    else
+        return (double)x;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real from_double(double x) {
+    if constexpr (std::is_same<Real, float>::value)
+        return d2f_rn(x);
+    else
+        return (Real)x;
+}
+
 template <typename Real, int STAGE>
 __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const UpdGeom<Real> &ug, int i, int j, int k,
                                             double dt) {
@@ -346,18 +389,18 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
         const Real dbx = -(ox_c - ox_jm) * ug.rdy + (oz_c - oz_km) * ug.rdz;
         const Real dby = -(oy_c - oy_km) * ug.rdz + (ox_c - ox_im) * ug.rdx;
         const Real dbz = -(oz_c - oz_im) * ug.rdx + (oy_c - oy_jm) * ug.rdy;
-        const Real cdt = (Real)(c * dt);
+        const Real cdt = from_double<Real>(c * dt);
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
             a.qs[f][p] = q0v[f] + cdt * D[f];
-            a.acc[f][p] = accv[f] + wc * (double)D[f];
+            a.acc[f][p] = accv[f] + wc * to_double(D[f]);
         }
         a.bs[0][p] = b0v[0] + cdt * dbx;
         a.bs[1][p] = b0v[1] + cdt * dby;
         a.bs[2][p] = b0v[2] + cdt * dbz;
-        a.oacc[0][p] = oav[0] + wc * (double)ox_c;
-        a.oacc[1][p] = oav[1] + wc * (double)oy_c;
-        a.oacc[2][p] = oav[2] + wc * (double)oz_c;
+        a.oacc[0][p] = oav[0] + wc * to_double(ox_c);
+        a.oacc[1][p] = oav[1] + wc * to_double(oy_c);
+        a.oacc[2][p] = oav[2] + wc * to_double(oz_c);
     } else {
         double q0v[5], b0v[3];
 #pragma unroll
@@ -366,15 +409,15 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
         for (int f = 0; f < 3; ++f) b0v[f] = a.b0[f][p];
         // accumulated EMFs sum_k w'_k Omega_k, in double, at the nine edges
         const double *Ax = a.oacc[0], *Ay = a.oacc[1], *Az = a.oacc[2];
-        const double ax_c = Ax[p] + wc * (double)ox_c;
-        const double ax_jm = Ax[p + ym] + wc * (double)ox_jm;
-        const double ax_im = Ax[p + xm] + wc * (double)ox_im;
-        const double ay_c = Ay[p] + wc * (double)oy_c;
-        const double ay_km = Ay[p + zm] + wc * (double)oy_km;
-        const double ay_jm = Ay[p + ym] + wc * (double)oy_jm;
-        const double az_c = Az[p] + wc * (double)oz_c;
-        const double az_km = Az[p + zm] + wc * (double)oz_km;
-        const double az_im = Az[p + xm] + wc * (double)oz_im;
+        const double ax_c = Ax[p] + wc * to_double(ox_c);
+        const double ax_jm = Ax[p + ym] + wc * to_double(ox_jm);
+        const double ax_im = Ax[p + xm] + wc * to_double(ox_im);
+        const double ay_c = Ay[p] + wc * to_double(oy_c);
+        const double ay_km = Ay[p + zm] + wc * to_double(oy_km);
+        const double ay_jm = Ay[p + ym] + wc * to_double(oy_jm);
+        const double az_c = Az[p] + wc * to_double(oz_c);
+        const double az_km = Az[p + zm] + wc * to_double(oz_km);
+        const double az_im = Az[p + xm] + wc * to_double(oz_im);
         const double dbx = -(ax_c - ax_jm) * ug.drdy + (az_c - az_km) * ug.drdz;
         const double dby = -(ay_c - ay_km) * ug.drdz + (ax_c - ax_im) * ug.drdx;
         const double dbz = -(az_c - az_im) * ug.drdx + (ay_c - ay_jm) * ug.drdy;
@@ -382,17 +425,19 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
         constexpr bool kCopy = !std::is_same<Real, double>::value;   // float copy of q^{n+1}, b^{n+1}
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
-            const double qn = q0v[f] + dt * (accv[f] + wc * (double)D[f]);
+            const double qn = q0v[f] + dt * (accv[f] + wc * to_double(D[f]));
+            const Real qr = from_double<Real>(qn);
             a.q0[f][p] = qn;
-            a.qs[f][p] = (Real)qn;
-            if (kCopy) a.q0r[f][p] = (Real)qn;
+            a.qs[f][p] = qr;
+            if (kCopy) a.q0r[f][p] = qr;
         }
         const double bn[3] = {b0v[0] + dt * dbx, b0v[1] + dt * dby, b0v[2] + dt * dbz};
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
+            const Real br = from_double<Real>(bn[f]);
             a.b0[f][p] = bn[f];
-            a.bs[f][p] = (Real)bn[f];
-            if (kCopy) a.b0r[f][p] = (Real)bn[f];
+            a.bs[f][p] = br;
+            if (kCopy) a.b0r[f][p] = br;
         }
     }
 }
