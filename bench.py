@@ -64,20 +64,32 @@ def load_peaks():
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=None, help="timed steps (default per workload)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--n", type=int, default=None, help="box edge (default per workload)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-n", type=int, default=64, help="edge of the oracle's sample box (reference arm)")
     p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave", "batched", "adjoint"],
-                   help="turb: 256^3 turbulence (default); blast: blast in Mach-5 turbulence (use --n 512); "
-                        "wave: the 32^3 fast eigenmode (use --n 32 --steps 20); batched: 512 uneven patches")
+                   help="turb: 256^3 turbulence, 50 steps (default); blast: 512^3 blast in Mach-5 turbulence, "
+                        "100 steps; wave: the 32^3 fast eigenmode, 20 steps; batched: 512 uneven patches, "
+                        "10 steps; adjoint: 64^3 rollout gradient, 10 steps")
     p.add_argument("--err-steps", type=int, default=5, help="FP64 steps of the blast error statement")
     p.add_argument("--patches", type=int, default=512, help="patches of the batched workload")
-    return p.parse_args(argv)
+    args = p.parse_args(argv)
+    n, steps = WORKLOAD_DEFAULTS[args.workload]
+    if args.n is None:
+        args.n = n
+    if args.steps is None:
+        args.steps = steps
+    return args
+
+
+# box edge and timed steps of each workload when not given
+WORKLOAD_DEFAULTS = {"turb": (256, 50), "blast": (512, 100), "wave": (32, 20), "batched": (256, 10),
+                     "adjoint": (64, 10)}
 
 
 def workload_config(n):

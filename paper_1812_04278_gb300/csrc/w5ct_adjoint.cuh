@@ -321,11 +321,11 @@ __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq
         const B xv[5] = {r, P, Bn, B1, B2};
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-            x[t] = D5((double)xv[t]);
+            x[t] = D5(xv[t]);
             x[t].d[t] = B(1);
         }
         const D5 irr = m5::rcp_(x[0]);
-        const D5 cs2 = D5((double)K.gamma) * x[1] * irr;
+        const D5 cs2 = D5(K.gamma) * x[1] * irr;
         const D5 ca2 = x[2] * x[2] * irr;
         const D5 bt2 = (x[3] * x[3] + x[4] * x[4]) * irr;
         D5 fmc, cms, cf2, csl2;
@@ -407,16 +407,16 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) in[s][5 + f] = a.bc[f][g];
     }
-    const A lam5 = (A)a.lamS[0][p], lam6 = (A)a.lamS[1][p];
+    const A lam5 = from_double<A>(a.lamS[0][p]), lam6 = from_double<A>(a.lamS[1][p]);
     // adjoint of the frame flux Ff (s1 = Ff[4] + bvt1, s2 = Ff[5] + bvt2)
     A lFf[7];
-    lFf[0] = (A)a.lamF[0][p];
-    lFf[1] = (A)a.lamF[1 + AX][p];
-    lFf[2] = (A)a.lamF[1 + (AX + 1) % 3][p];
-    lFf[3] = (A)a.lamF[1 + (AX + 2) % 3][p];
+    lFf[0] = from_double<A>(a.lamF[0][p]);
+    lFf[1] = from_double<A>(a.lamF[1 + AX][p]);
+    lFf[2] = from_double<A>(a.lamF[1 + (AX + 1) % 3][p]);
+    lFf[3] = from_double<A>(a.lamF[1 + (AX + 2) % 3][p]);
     lFf[4] = (A)lam5;
     lFf[5] = (A)lam6;
-    lFf[6] = (A)a.lamF[4][p];
+    lFf[6] = from_double<A>(a.lamF[4][p]);
     const Phys<B> K = a.K;
     bool bad = false, hit = false;
     B cq[NCQ * 6];
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
     const int prim[8] = {C_RHO, C_VN, C_VT1, C_VT2, C_BN, C_BT1, C_BT2, C_P};
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        wd[t] = D8((double)(B(0.5) * (Q(prim[t], 2) + Q(prim[t], 3))));
+        wd[t] = D8(B(B(0.5) * (Q(prim[t], 2) + Q(prim[t], 3))));
         wd[t].d[t] = B(1);
     }
     D8 Ld[7][7], Rd[7][7];
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
         A g[8];
         cell_fill_adjoint<B, A, AX>(in[c], lq[c], K, g);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) a.cb[(size_t)(c * 8 + v) * (size_t)n + (size_t)p] = (double)g[v];
+        for (int v = 0; v < 8; ++v) a.cb[(size_t)(c * 8 + v) * (size_t)n + (size_t)p] = to_double(g[v]);
     }
 }
 

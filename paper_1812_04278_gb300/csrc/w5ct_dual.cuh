@@ -12,6 +12,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "w5ct_physics.cuh"
 
 namespace w5ct {
@@ -22,6 +24,13 @@ struct Dual {
     T d[N];
     __device__ __forceinline__ Dual() {}
     __device__ __forceinline__ Dual(double c) : v((T)c) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) d[i] = T(0);
+    }
+    // a constant of the base type itself (no detour through double)
+    template <typename U, typename std::enable_if<std::is_same<U, T>::value && !std::is_same<T, double>::value,
+                                                  int>::type = 0>
+    __device__ __forceinline__ Dual(U c) : v(c) {
 #pragma unroll
         for (int i = 0; i < N; ++i) d[i] = T(0);
     }
@@ -159,16 +168,16 @@ struct M<Dual<T, N>> {
 template <typename T, int N>
 __device__ __forceinline__ Phys<Dual<T, N>> promote(const Phys<T> &K) {
     Phys<Dual<T, N>> D;
-    D.gamma = Dual<T, N>((double)K.gamma);
-    D.gm1 = Dual<T, N>((double)K.gm1);
-    D.g1 = Dual<T, N>((double)K.g1);
-    D.g2 = Dual<T, N>((double)K.g2);
-    D.eps_w = Dual<T, N>((double)K.eps_w);
-    D.eps_b = Dual<T, N>((double)K.eps_b);
-    D.eps_b2 = Dual<T, N>((double)K.eps_b2);
-    D.rho_min = Dual<T, N>((double)K.rho_min);
-    D.p_min = Dual<T, N>((double)K.p_min);
-    D.cs2_rel = Dual<T, N>((double)K.cs2_rel);
+    D.gamma = Dual<T, N>(K.gamma);
+    D.gm1 = Dual<T, N>(K.gm1);
+    D.g1 = Dual<T, N>(K.g1);
+    D.g2 = Dual<T, N>(K.g2);
+    D.eps_w = Dual<T, N>(K.eps_w);
+    D.eps_b = Dual<T, N>(K.eps_b);
+    D.eps_b2 = Dual<T, N>(K.eps_b2);
+    D.rho_min = Dual<T, N>(K.rho_min);
+    D.p_min = Dual<T, N>(K.p_min);
+    D.cs2_rel = Dual<T, N>(K.cs2_rel);
     D.floors = K.floors;
     return D;
 }
