@@ -177,7 +177,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "6dbc51cd8be9deaa", "fp64": 104.35, "fp32": 44.66}
+SWEEP_TRAFFIC = {"src": "35817d49d2df597b", "fp64": 104.41, "fp32": 44.46}
 
 
 def hbm_gbs(traffic, launch_ms):
