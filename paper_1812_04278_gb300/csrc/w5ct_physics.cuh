@@ -313,6 +313,87 @@ __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real ep
     }
 }
 
+// ---------------------------------------------------------------- float
+// In float the 11 stencil vectors are kept as the central one, X0, and the
+// five pairs X2[j] = (dF_j, du_j) (vectors 1 + j and 6 + j), which share
+// every projection coefficient: one packed two-lane FMA (sm_100 f32x2)
+// projects both.  Each lane rounds exactly as the scalar FMA would.
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// P = sum_k L[k] X[ci[k]] for the 11 vectors (scalar central, packed pairs)
+template <int N>
+__device__ __forceinline__ void project_f(const float (&X0)[7], const float2 (&X2)[5][7], const int (&ci)[N],
+                                          const float (&L)[N], float &P0, float2 (&P2)[5]) {
+    float p = L[0] * X0[ci[0]];
+#pragma unroll
+    for (int k = 1; k < N; ++k) p = __fmaf_rn(L[k], X0[ci[k]], p);
+    P0 = p;
+    float2 Lb[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) Lb[k] = bcast2(L[k]);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        float2 q = __fmul2_rn(Lb[0], X2[j][ci[0]]);
+#pragma unroll
+        for (int k = 1; k < N; ++k) q = __ffma2_rn(Lb[k], X2[j][ci[k]], q);
+        P2[j] = q;
+    }
+}
+
+// weno_field's 11 projections from the central value and the five pairs
+__device__ __forceinline__ void unpack11(float P0, const float2 (&P2)[5], float (&P)[11]) {
+    P[0] = P0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        P[1 + j] = P2[j].x;
+        P[6 + j] = P2[j].y;
+    }
+}
+
+// (P_c + P_s, P_c - P_s) of a mode pair, both packed halves at once
+__device__ __forceinline__ void split_pair_f(float Pc0, const float2 (&Pc2)[5], float Ps0, const float2 (&Ps2)[5],
+                                             float (&Pu)[11], float (&Pl)[11]) {
+    float2 U[5], D[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        U[j] = __fadd2_rn(Pc2[j], Ps2[j]);
+        D[j] = __fadd2_rn(Pc2[j], neg2(Ps2[j]));
+    }
+    unpack11(Pc0 + Ps0, U, Pu);
+    unpack11(Pc0 - Ps0, D, Pl);
+}
+
+// magnetosonic_pair (below) with the float packed projection
+template <int VAR>
+__device__ __forceinline__ void magnetosonic_pair_f(const float (&X0)[7], const float2 (&X2)[5][7],
+                                                    const float (&Lc)[7], const float (&Ls)[4], const float (&Rc)[7],
+                                                    const float (&Rs)[4], float alu, float all, float eps,
+                                                    float (&Ff)[7], bool first) {
+    constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
+    constexpr int cs[4] = {0, 1, 2, 3};
+    float pc0, ps0;
+    float2 pc2[5], ps2[5];
+    project_f<7>(X0, X2, cc, Lc, pc0, pc2);
+    project_f<4>(X0, X2, cs, Ls, ps0, ps2);
+    float Pu[11], Pl[11];
+    split_pair_f(pc0, pc2, ps0, ps2, Pu, Pl);
+    const float Fu = weno_field<float, VAR>(Pu, alu, eps);
+    const float Fl = weno_field<float, VAR>(Pl, all, eps);
+    const float sum = Fu + Fl, dif = Fu - Fl;
+    if (first) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Ff[c] = sum * Rc[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Ff[c] += sum * Rc[c];
+    }
+    Ff[1] += dif * Rs[0];
+    Ff[2] += dif * Rs[1];
+    Ff[3] += dif * Rs[2];
+    Ff[6] += dif * Rs[3];
+}
+
 // One magnetosonic (fast or slow) pair of characteristic fields: the left
 // eigenvectors are Lc + Ls and Lc - Ls (Ls non-zero in rows 0..3), the right
 // ones Rc + Rs and Rc - Rs (Rs non-zero in rows 1, 2, 3, 6).  The first
@@ -378,6 +459,18 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         X[8][c] = u3 - u2;
         X[9][c] = u4 - u3;
         X[10][c] = u5 - u4;
+    }
+    // float: the central vector and the pairs (dF_j, du_j) for the packed
+    // projection (the same values; only their grouping)
+    [[maybe_unused]] float X0f[7];
+    [[maybe_unused]] float2 X2f[5][7];
+    if constexpr (std::is_same<Real, float>::value) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            X0f[c] = X[0][c];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) X2f[j][c] = make_float2(X[1 + j][c], X[6 + j][c]);
+        }
     }
     // interface state: mean of the primitives of cells i and i+1
     const Real r = Real(0.5) * (SMQ(C_RHO, 2) + SMQ(C_RHO, 3));
@@ -463,7 +556,10 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         const Real Rc[7] = {af, af * vn, af * vt1, af * vt2, cs * as * b1 * isr, cs * as * b2 * isr,
                             af * (Real(0.5) * v2 + cf2 - K.g2 * cs2)};
         const Real Rs[4] = {-af * cf, csl * as * b1 * sg, csl * as * b2 * sg, -Gf};   // rows 1, 2, 3, 6
-        magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
+        if constexpr (std::is_same<Real, float>::value)
+            magnetosonic_pair_f<VAR>(X0f, X2f, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
+        else
+            magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
     }
     // ---- slow pair: m = 3 (v - c_slow, upper sign) and m = 5 (v + c_slow)
     {
@@ -474,7 +570,10 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         const Real Rc[7] = {as, as * vn, as * vt1, as * vt2, -cs * af * b1 * isr, -cs * af * b2 * isr,
                             as * (Real(0.5) * v2 + csl2 - K.g2 * cs2)};
         const Real Rs[4] = {-as * csl, -cf * af * b1 * sg, -cf * af * b2 * sg, -Gs};
-        magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
+        if constexpr (std::is_same<Real, float>::value)
+            magnetosonic_pair_f<VAR>(X0f, X2f, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
+        else
+            magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
     }
     // ---- Alfven pair: m = 2 (v - c_A, upper sign) and m = 6 (v + c_A)
     {
@@ -483,12 +582,23 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         const Real l0 = Real(0.5) * Ga, l2 = Real(-0.5) * b2 * sg, l3 = Real(0.5) * b1 * sg;
         const Real l4 = Real(-0.5) * sr * b2, l5 = Real(0.5) * sr * b1;
         Real Pu[11], Pl[11];
+        if constexpr (std::is_same<Real, float>::value) {
+            constexpr int cc[3] = {0, 2, 3};
+            constexpr int cs[2] = {4, 5};
+            const float Lc[3] = {l0, l2, l3}, Ls[2] = {l4, l5};
+            float pc0, ps0;
+            float2 pc2[5], ps2[5];
+            project_f<3>(X0f, X2f, cc, Lc, pc0, pc2);
+            project_f<2>(X0f, X2f, cs, Ls, ps0, ps2);
+            split_pair_f(pc0, pc2, ps0, ps2, Pu, Pl);
+        } else {
 #pragma unroll
-        for (int x = 0; x < 11; ++x) {
-            const Real pc = l0 * X[x][0] + l2 * X[x][2] + l3 * X[x][3];
-            const Real ps = l4 * X[x][4] + l5 * X[x][5];
-            Pu[x] = pc + ps;
-            Pl[x] = pc - ps;
+            for (int x = 0; x < 11; ++x) {
+                const Real pc = l0 * X[x][0] + l2 * X[x][2] + l3 * X[x][3];
+                const Real ps = l4 * X[x][4] + l5 * X[x][5];
+                Pu[x] = pc + ps;
+                Pl[x] = pc - ps;
+            }
         }
         const Real Fu = weno_field<Real, VAR>(Pu, al_am, eps);
         const Real Fl = weno_field<Real, VAR>(Pl, al_ap, eps);
@@ -503,12 +613,20 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     {
         const Real L[7] = {Real(1) - Real(0.5) * tau * v2, tau * vn, tau * vt1, tau * vt2, tau * Bt1, tau * Bt2, -tau};
         Real Pe[11];
+        if constexpr (std::is_same<Real, float>::value) {
+            constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
+            float pe0;
+            float2 pe2[5];
+            project_f<7>(X0f, X2f, cc, L, pe0, pe2);
+            unpack11(pe0, pe2, Pe);
+        } else {
 #pragma unroll
-        for (int x = 0; x < 11; ++x) {
-            Real pc = L[0] * X[x][0];
+            for (int x = 0; x < 11; ++x) {
+                Real pc = L[0] * X[x][0];
 #pragma unroll
-            for (int c = 1; c < 7; ++c) pc += L[c] * X[x][c];
-            Pe[x] = pc;
+                for (int c = 1; c < 7; ++c) pc += L[c] * X[x][c];
+                Pe[x] = pc;
+            }
         }
         const Real Fe = weno_field<Real, VAR>(Pe, al_e, eps);
         Ff[0] += Fe;
