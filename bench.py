@@ -177,7 +177,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "35817d49d2df597b", "fp64": 104.41, "fp32": 44.46}
+SWEEP_TRAFFIC = {"src": "e68a73d1f3c65215", "fp64": 104.61, "fp32": 44.81}
 
 
 def hbm_gbs(traffic, launch_ms):
