@@ -250,3 +250,42 @@ def test_fp32_bulk_one_step_near_oracle(env, variant):
     linf, _ = s.div_b_norm()
     assert linf < 1e-12
     s.close()
+
+
+def degenerate_field_state(env, shape, B, seed):
+    """Smooth density, pressure and velocity with a uniform field B: B = 0
+    (no magnetic waves: c_A = c_slow = 0, the B_t direction undefined) or
+    B along x with c_A > c_s (on x faces B_t = 0, so c_f = c_A and the
+    fast/slow normalisations degenerate; on y and z faces B_n = 0)."""
+    I = env["I"]
+    X, Y, Z, _ = I.cell_centres(shape)
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 2 * np.pi, 8)
+    tp = 2 * np.pi
+    rho = 1.0 + 0.2 * np.sin(tp * X + a[0]) * np.cos(tp * Y + a[1]) + 0.1 * np.sin(tp * Z + a[2])
+    P = 0.6 * (1.0 + 0.2 * np.cos(tp * (X + Y) + a[3]) + 0.1 * np.sin(tp * Z + a[4]))
+    v = 0.3 * np.stack([np.sin(tp * Y + a[5]), np.cos(tp * Z + a[6]), np.sin(tp * X + a[7])])
+    o = np.ones(rho.shape)
+    bface = np.stack([o * B[0], o * B[1], o * B[2]])
+    return I.assemble(rho, v, P, bface, Bc=bface.copy())
+
+
+@pytest.mark.parametrize("B,why", [((0.0, 0.0, 0.0), "no field"), ((2.0, 0.0, 0.0), "field along x, c_A > c_s")])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp64_degenerate_field_states_match_oracle(env, B, why, variant):
+    """The eigenvector branches of Appendix A for B = 0 and B_t = 0 (the
+    epsilon_B switches and the degenerate fast/slow normalisations): two
+    steps equal the oracle to 1e-12 per step, each from identical input."""
+    shape = (20, 12, 16)
+    dx = tuple(1.0 / n for n in shape)
+    cons, bface = degenerate_field_state(env, shape, B, seed=31 + variant)
+    s, o = make_pair(env, shape, dx, cons, bface, variant=variant)
+    for _ in range(2):
+        dt = o.cfl_dt()
+        c0, b0, _ = o.get_state()
+        s.set_state(c0, b0)
+        s.step(dt)
+        o.step(dt)
+        rel_s, rel_f = compare(s.get_state(), o.get_state())
+        assert rel_s.max() <= TOL64, (why, rel_s)
+    s.close()
