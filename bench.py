@@ -142,7 +142,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
@@ -153,6 +153,10 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
@@ -160,7 +164,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": float(np.median(pw)) if pw else None}
 
 
 # ------------------------------------------------------------------ helpers
@@ -389,12 +393,16 @@ def run_native(args):
     torch.cuda.synchronize()
     if barrier:
         barrier()
+    e2e_sampler = ClockSampler(local) if rank == 0 else None
+    if e2e_sampler:
+        e2e_sampler.start()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         w5.w5ct_set_state(se.ctx, hc.data_ptr(), hb.data_ptr(), 0)
         se.step_cfl()
         w5.w5ct_get_state(se.ctx, oc.data_ptr(), ob.data_ptr(), None, 0)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_clocks = e2e_sampler.stop() if e2e_sampler else None
     se.close()
 
     if rank != 0:
@@ -453,7 +461,8 @@ def run_native(args):
         "conservation_drift": drift64,
         "e2e": {"value": world * zones * e2e_steps / e2e_s, "unit": "zone-updates/s",
                 "h2d_bytes_per_step": int(cons.nbytes + bface.nbytes),
-                "d2h_bytes_per_step": int(cons.nbytes + bface.nbytes), "steps": e2e_steps},
+                "d2h_bytes_per_step": int(cons.nbytes + bface.nbytes), "steps": e2e_steps,
+                "clocks": e2e_clocks},
         "gpu_launches": launches64,
         "clocks": clocks,
         "kernel_src": kernel_source_hash(),
