@@ -152,6 +152,459 @@ __device__ __forceinline__ void eigen7(const Real (&w)[8], const Phys<Real> &K, 
     }
 }
 
+// Reverse of speeds(): adds to (lcs2, lca2, lbt2) the adjoints of its inputs
+// given those of (fmc, cms, cf2, csl2); the same branches and guards as the
+// forward formulas (Eqs. slow/fast), run backwards.
+template <typename B, typename A>
+__device__ __forceinline__ void speeds_rev(B cs2, B ca2, B bt2, A lfmc, A lcms, A lcf2, A lcsl2, A &lcs2, A &lca2,
+                                           A &lbt2) {
+    using m = M<B>;
+    const B dd = (cs2 - ca2) * (cs2 - ca2) + bt2 * (bt2 + B(2) * ca2 + B(2) * cs2);
+    const B sd = m::sqrt_(dd);
+    const B aa = ca2 + bt2 - cs2;
+    B fmc, cms;
+    if (aa >= B(0)) {
+        fmc = B(0.5) * (aa + sd);
+        cms = fmc > B(0) ? m::div_(cs2 * bt2, fmc) : B(0);
+    } else {
+        cms = B(0.5) * (sd - aa);
+        fmc = cms > B(0) ? m::div_(cs2 * bt2, cms) : B(0);
+    }
+    const B cf2 = cs2 + fmc;
+    if (cf2 > B(0)) {
+        const A icf = A(1) / (A)cf2;
+        const A csl2 = (A)m::div_(cs2 * ca2, cf2);
+        lcs2 += lcsl2 * (A)ca2 * icf;
+        lca2 += lcsl2 * (A)cs2 * icf;
+        lcf2 -= lcsl2 * csl2 * icf;
+    }
+    lcs2 += lcf2;
+    lfmc += lcf2;
+    A laa = A(0), lsd = A(0);
+    if (aa >= B(0)) {
+        if (fmc > B(0)) {
+            const A ifm = A(1) / (A)fmc;
+            lcs2 += lcms * (A)bt2 * ifm;
+            lbt2 += lcms * (A)cs2 * ifm;
+            lfmc -= lcms * (A)cms * ifm;
+        }
+        laa += A(0.5) * lfmc;
+        lsd += A(0.5) * lfmc;
+    } else {
+        if (cms > B(0)) {
+            const A icm = A(1) / (A)cms;
+            lcs2 += lfmc * (A)bt2 * icm;
+            lbt2 += lfmc * (A)cs2 * icm;
+            lcms -= lfmc * (A)fmc * icm;
+        }
+        lsd += A(0.5) * lcms;
+        laa -= A(0.5) * lcms;
+    }
+    lca2 += laa;
+    lbt2 += laa;
+    lcs2 -= laa;
+    const A ldd = sd > B(0) ? lsd * A(0.5) / (A)sd : A(0);
+    lcs2 += ldd * (A(2) * ((A)cs2 - (A)ca2) + A(2) * (A)bt2);
+    lca2 += ldd * (A(-2) * ((A)cs2 - (A)ca2) + A(2) * (A)bt2);
+    lbt2 += ldd * (A(2) * (A)bt2 + A(2) * (A)ca2 + A(2) * (A)cs2);
+}
+
+// Reverse of eigen7: lw = d/dw of sum(lL * L) + sum(lR * R) at the
+// interface state w, written by hand from the forward formulas (recomputed
+// here in B; the adjoints in A).  Branches follow the primal values: the
+// epsilon_B switches and the WENO sign sg, the c_s^2 bound of the float
+// path, the sqrt of zero (subgradient 0) -- the same choices the
+// dual-number form of eigen7 makes.
+template <typename B, typename A>
+__device__ __forceinline__ void eigen7_rev(const B (&w)[8], const Phys<B> &K, const A (&lL)[7][7], const A (&lR)[7][7],
+                                           A (&lw)[8]) {
+    using m = M<B>;
+    const B r = w[0], vn = w[1], vt1 = w[2], vt2 = w[3], Bn = w[4], Bt1 = w[5], Bt2 = w[6], P = w[7];
+    // ---- forward values
+    const B ir = m::rcp_(r);
+    const B ca2 = Bn * Bn * ir;
+    const B btm = Bt1 * Bt1 + Bt2 * Bt2;
+    const B bt2 = btm * ir;
+    const B v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    const B cs2a = K.gamma * P * ir;
+    B cs2 = cs2a;
+    bool bound = false;
+    if constexpr (float_based<B>) {
+        const B cs2b = K.cs2_rel * (v2 + ca2 + bt2);
+        bound = cs2b > cs2a;
+        cs2 = m::max_(cs2a, cs2b);
+    }
+    B fmc, cms, cf2, csl2;
+    speeds<B>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+    const B cf = m::sqrt_(cf2), csl = m::sqrt_(csl2), cs = m::sqrt_(cs2);
+    const B dfs = fmc + cms;
+    const bool brA = dfs >= K.eps_b2;
+    B af = B(1), as = B(1), idf = B(0), qa = B(0), qs = B(0);
+    if (brA) {
+        idf = m::rcp_(dfs);
+        qa = cms * idf;
+        qs = fmc * idf;
+        af = m::sqrt_(m::max_(qa, B(0)));
+        as = m::sqrt_(m::max_(qs, B(0)));
+    }
+    const bool brB = btm > K.eps_b;
+    B b1 = B(0.70710678118654752440), b2 = B(0.70710678118654752440), ib = B(0);
+    if (brB) {
+        ib = m::rsqrt_(btm);
+        b1 = Bt1 * ib;
+        b2 = Bt2 * ib;
+    }
+    const A sg = (Bn >= K.eps_b) ? A(1) : A(-1);
+    const B sr = m::sqrt_(r);
+    const B isr = sr * ir;
+    const B bvB = b1 * vt1 + b2 * vt2;
+    const B ics2B = m::rcp_(cs2);
+    // the rest in the adjoint type
+    const A Ar = (A)r, Avn = (A)vn, Avt1 = (A)vt1, Avt2 = (A)vt2, ABt1 = (A)Bt1, ABt2 = (A)Bt2;
+    const A Av2 = (A)v2, Acf = (A)cf, Acsl = (A)csl, Acs = (A)cs, Acf2 = (A)cf2, Acsl2 = (A)csl2, Acs2 = (A)cs2;
+    const A Aaf = (A)af, Aas = (A)as, Ab1 = (A)b1, Ab2 = (A)b2, Asr = (A)sr, Aisr = (A)isr, Abv = (A)bvB;
+    const A ics2 = (A)ics2B, pre = A(0.5) * ics2, gm1 = (A)K.gm1, g1 = (A)K.g1, g2 = (A)K.g2;
+    const A tau = gm1 * ics2;
+    const A Gf = Aaf * Acf * Avn - Aas * Acsl * sg * Abv;
+    const A Gs = Aas * Acsl * Avn + Aaf * Acf * sg * Abv;
+    const A k1 = -gm1 * Aaf, k2 = -gm1 * Aas;
+    const A V[3] = {Avn, Avt1, Avt2};
+    (void)Ar;
+    // ---- adjoints
+    A lpre = 0, laf = 0, las = 0, lcf = 0, lcsl = 0, lcs = 0, lsr = 0, lisr = 0, lb1 = 0, lb2 = 0;
+    A lGf = 0, lGs = 0, lGa = 0, lv2 = 0, lBt1 = 0, lBt2 = 0, lcf2 = 0, lcsl2 = 0, lcs2 = 0, ltau = 0;
+    A lk1 = 0, lk2 = 0;
+    A lv[3] = {0, 0, 0};
+    // fast pair (modes 0, 1): L = Lc +- Ls, R = Rc +- Rs (rows 1, 2, 3, 6)
+    {
+        A lLc[7], lLs[4], lRc[7], lRs[4];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            lLc[c] = lL[0][c] + lL[1][c];
+            lRc[c] = lR[0][c] + lR[1][c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lLs[c] = lL[0][c] - lL[1][c];
+        lRs[0] = lR[0][1] - lR[1][1];
+        lRs[1] = lR[0][2] - lR[1][2];
+        lRs[2] = lR[0][3] - lR[1][3];
+        lRs[3] = lR[0][6] - lR[1][6];
+        A l = lLc[0];
+        lpre += l * g1 * Aaf * Av2;
+        laf += l * pre * g1 * Av2;
+        lv2 += l * pre * g1 * Aaf;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            l = lLc[1 + j];
+            lpre += l * k1 * V[j];
+            lk1 += l * pre * V[j];
+            lv[j] += l * pre * k1;
+        }
+        {
+            l = lLc[4];
+            const A lt = l * pre;
+            lpre += l * (k1 * ABt1 + Asr * Acs * Aas * Ab1);
+            lk1 += lt * ABt1;
+            lBt1 += lt * k1;
+            lsr += lt * Acs * Aas * Ab1;
+            lcs += lt * Asr * Aas * Ab1;
+            las += lt * Asr * Acs * Ab1;
+            lb1 += lt * Asr * Acs * Aas;
+        }
+        {
+            l = lLc[5];
+            const A lt = l * pre;
+            lpre += l * (k1 * ABt2 + Asr * Acs * Aas * Ab2);
+            lk1 += lt * ABt2;
+            lBt2 += lt * k1;
+            lsr += lt * Acs * Aas * Ab2;
+            lcs += lt * Asr * Aas * Ab2;
+            las += lt * Asr * Acs * Ab2;
+            lb2 += lt * Asr * Acs * Aas;
+        }
+        l = lLc[6];
+        lpre += l * gm1 * Aaf;
+        laf += l * pre * gm1;
+        l = lLs[0];
+        lpre += l * Gf;
+        lGf += l * pre;
+        l = lLs[1];
+        lpre -= l * Aaf * Acf;
+        laf -= l * pre * Acf;
+        lcf -= l * pre * Aaf;
+        l = lLs[2];
+        lpre += l * Acsl * Aas * Ab1 * sg;
+        lcsl += l * pre * Aas * Ab1 * sg;
+        las += l * pre * Acsl * Ab1 * sg;
+        lb1 += l * pre * Acsl * Aas * sg;
+        l = lLs[3];
+        lpre += l * Acsl * Aas * Ab2 * sg;
+        lcsl += l * pre * Aas * Ab2 * sg;
+        las += l * pre * Acsl * Ab2 * sg;
+        lb2 += l * pre * Acsl * Aas * sg;
+        laf += lRc[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            l = lRc[1 + j];
+            laf += l * V[j];
+            lv[j] += l * Aaf;
+        }
+        l = lRc[4];
+        lcs += l * Aas * Ab1 * Aisr;
+        las += l * Acs * Ab1 * Aisr;
+        lb1 += l * Acs * Aas * Aisr;
+        lisr += l * Acs * Aas * Ab1;
+        l = lRc[5];
+        lcs += l * Aas * Ab2 * Aisr;
+        las += l * Acs * Ab2 * Aisr;
+        lb2 += l * Acs * Aas * Aisr;
+        lisr += l * Acs * Aas * Ab2;
+        l = lRc[6];
+        laf += l * (A(0.5) * Av2 + Acf2 - g2 * Acs2);
+        lv2 += l * Aaf * A(0.5);
+        lcf2 += l * Aaf;
+        lcs2 -= l * Aaf * g2;
+        l = lRs[0];
+        laf -= l * Acf;
+        lcf -= l * Aaf;
+        l = lRs[1];
+        lcsl += l * Aas * Ab1 * sg;
+        las += l * Acsl * Ab1 * sg;
+        lb1 += l * Acsl * Aas * sg;
+        l = lRs[2];
+        lcsl += l * Aas * Ab2 * sg;
+        las += l * Acsl * Ab2 * sg;
+        lb2 += l * Acsl * Aas * sg;
+        lGf -= lRs[3];
+        laf -= gm1 * lk1;
+    }
+    // slow pair (modes 2, 3)
+    {
+        A lLc[7], lLs[4], lRc[7], lRs[4];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            lLc[c] = lL[2][c] + lL[3][c];
+            lRc[c] = lR[2][c] + lR[3][c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) lLs[c] = lL[2][c] - lL[3][c];
+        lRs[0] = lR[2][1] - lR[3][1];
+        lRs[1] = lR[2][2] - lR[3][2];
+        lRs[2] = lR[2][3] - lR[3][3];
+        lRs[3] = lR[2][6] - lR[3][6];
+        A l = lLc[0];
+        lpre += l * g1 * Aas * Av2;
+        las += l * pre * g1 * Av2;
+        lv2 += l * pre * g1 * Aas;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            l = lLc[1 + j];
+            lpre += l * k2 * V[j];
+            lk2 += l * pre * V[j];
+            lv[j] += l * pre * k2;
+        }
+        {
+            l = lLc[4];
+            const A lt = l * pre;
+            lpre += l * (k2 * ABt1 - Asr * Acs * Aaf * Ab1);
+            lk2 += lt * ABt1;
+            lBt1 += lt * k2;
+            lsr -= lt * Acs * Aaf * Ab1;
+            lcs -= lt * Asr * Aaf * Ab1;
+            laf -= lt * Asr * Acs * Ab1;
+            lb1 -= lt * Asr * Acs * Aaf;
+        }
+        {
+            l = lLc[5];
+            const A lt = l * pre;
+            lpre += l * (k2 * ABt2 - Asr * Acs * Aaf * Ab2);
+            lk2 += lt * ABt2;
+            lBt2 += lt * k2;
+            lsr -= lt * Acs * Aaf * Ab2;
+            lcs -= lt * Asr * Aaf * Ab2;
+            laf -= lt * Asr * Acs * Ab2;
+            lb2 -= lt * Asr * Acs * Aaf;
+        }
+        l = lLc[6];
+        lpre += l * gm1 * Aas;
+        las += l * pre * gm1;
+        l = lLs[0];
+        lpre += l * Gs;
+        lGs += l * pre;
+        l = lLs[1];
+        lpre -= l * Aas * Acsl;
+        las -= l * pre * Acsl;
+        lcsl -= l * pre * Aas;
+        l = lLs[2];
+        lpre -= l * Acf * Aaf * Ab1 * sg;
+        lcf -= l * pre * Aaf * Ab1 * sg;
+        laf -= l * pre * Acf * Ab1 * sg;
+        lb1 -= l * pre * Acf * Aaf * sg;
+        l = lLs[3];
+        lpre -= l * Acf * Aaf * Ab2 * sg;
+        lcf -= l * pre * Aaf * Ab2 * sg;
+        laf -= l * pre * Acf * Ab2 * sg;
+        lb2 -= l * pre * Acf * Aaf * sg;
+        las += lRc[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            l = lRc[1 + j];
+            las += l * V[j];
+            lv[j] += l * Aas;
+        }
+        l = lRc[4];
+        lcs -= l * Aaf * Ab1 * Aisr;
+        laf -= l * Acs * Ab1 * Aisr;
+        lb1 -= l * Acs * Aaf * Aisr;
+        lisr -= l * Acs * Aaf * Ab1;
+        l = lRc[5];
+        lcs -= l * Aaf * Ab2 * Aisr;
+        laf -= l * Acs * Ab2 * Aisr;
+        lb2 -= l * Acs * Aaf * Aisr;
+        lisr -= l * Acs * Aaf * Ab2;
+        l = lRc[6];
+        las += l * (A(0.5) * Av2 + Acsl2 - g2 * Acs2);
+        lv2 += l * Aas * A(0.5);
+        lcsl2 += l * Aas;
+        lcs2 -= l * Aas * g2;
+        l = lRs[0];
+        las -= l * Acsl;
+        lcsl -= l * Aas;
+        l = lRs[1];
+        lcf -= l * Aaf * Ab1 * sg;
+        laf -= l * Acf * Ab1 * sg;
+        lb1 -= l * Acf * Aaf * sg;
+        l = lRs[2];
+        lcf -= l * Aaf * Ab2 * sg;
+        laf -= l * Acf * Ab2 * sg;
+        lb2 -= l * Acf * Aaf * sg;
+        lGs -= lRs[3];
+        las -= gm1 * lk2;
+    }
+    // Alfven pair (modes 4, 5)
+    {
+        const A ll0 = lL[4][0] + lL[5][0], ll2 = lL[4][2] + lL[5][2], ll3 = lL[4][3] + lL[5][3];
+        const A ll4 = lL[4][4] - lL[5][4], ll5 = lL[4][5] - lL[5][5];
+        lGa += A(0.5) * ll0;
+        lb2 -= A(0.5) * sg * ll2;
+        lb1 += A(0.5) * sg * ll3;
+        lsr -= A(0.5) * Ab2 * ll4;
+        lb2 -= A(0.5) * Asr * ll4;
+        lsr += A(0.5) * Ab1 * ll5;
+        lb1 += A(0.5) * Asr * ll5;
+        const A r2 = lR[4][2] + lR[5][2], r3 = lR[4][3] + lR[5][3], r4 = lR[4][4] - lR[5][4];
+        const A r5 = lR[4][5] - lR[5][5], r6 = lR[4][6] + lR[5][6];
+        lb2 -= sg * r2;
+        lb1 += sg * r3;
+        lb2 -= Aisr * r4;
+        lisr -= Ab2 * r4;
+        lb1 += Aisr * r5;
+        lisr += Ab1 * r5;
+        lGa -= r6;
+    }
+    // entropy (mode 6)
+    {
+        A l = lL[6][0];
+        ltau -= A(0.5) * Av2 * l;
+        lv2 -= A(0.5) * tau * l;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            l = lL[6][1 + j];
+            ltau += l * V[j];
+            lv[j] += l * tau;
+        }
+        ltau += lL[6][4] * ABt1;
+        lBt1 += lL[6][4] * tau;
+        ltau += lL[6][5] * ABt2;
+        lBt2 += lL[6][5] * tau;
+        ltau -= lL[6][6];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) lv[j] += lR[6][1 + j];
+        lv2 += A(0.5) * lR[6][6];
+    }
+    // ---- the scalars, backwards
+    const A lics2 = gm1 * ltau + A(0.5) * lpre;
+    lcs2 -= ics2 * (ics2 * lics2);
+    las += lGs * Acsl * Avn;
+    lcsl += lGs * Aas * Avn;
+    lv[0] += lGs * Aas * Acsl;
+    laf += lGs * Acf * sg * Abv;
+    lcf += lGs * Aaf * sg * Abv;
+    A lbv = lGs * Aaf * Acf * sg;
+    // Ga = sg (b2 vt1 - b1 vt2)
+    lb2 += lGa * sg * Avt1;
+    lv[1] += lGa * sg * Ab2;
+    lb1 -= lGa * sg * Avt2;
+    lv[2] -= lGa * sg * Ab1;
+    laf += lGf * Acf * Avn;
+    lcf += lGf * Aaf * Avn;
+    lv[0] += lGf * Aaf * Acf;
+    las -= lGf * Acsl * sg * Abv;
+    lcsl -= lGf * Aas * sg * Abv;
+    lbv -= lGf * Aas * Acsl * sg;
+    lb1 += lbv * Avt1;
+    lv[1] += lbv * Ab1;
+    lb2 += lbv * Avt2;
+    lv[2] += lbv * Ab2;
+    const A Air = (A)ir;
+    A lir = lisr * Asr;
+    lsr += lisr * Air;
+    A lr = sr > B(0) ? lsr * A(0.5) / Asr : A(0);
+    A lbtm = A(0);
+    if (brB) {
+        const A Aib = (A)ib;
+        lBt1 += lb1 * Aib;
+        lBt2 += lb2 * Aib;
+        const A lib = lb1 * ABt1 + lb2 * ABt2;
+        lbtm -= A(0.5) * Aib * (Aib * (Aib * lib));
+    }
+    A lfmc = A(0), lcms = A(0);
+    if (brA) {
+        const A lqa = qa > B(0) ? laf * A(0.5) / Aaf : A(0);
+        const A lqs = qs > B(0) ? las * A(0.5) / Aas : A(0);
+        const A Aidf = (A)idf;
+        lcms += lqa * Aidf;
+        lfmc += lqs * Aidf;
+        const A lidf = lqa * (A)cms + lqs * (A)fmc;
+        const A ldfs = -Aidf * (Aidf * lidf);
+        lfmc += ldfs;
+        lcms += ldfs;
+    }
+    if (cs > B(0)) lcs2 += lcs * A(0.5) / Acs;
+    if (csl > B(0)) lcsl2 += lcsl * A(0.5) / Acsl;
+    if (cf > B(0)) lcf2 += lcf * A(0.5) / Acf;
+    A lca2 = A(0), lbt2 = A(0);
+    speeds_rev<B, A>(cs2, ca2, bt2, lfmc, lcms, lcf2, lcsl2, lcs2, lca2, lbt2);
+    A lP = A(0);
+    if (bound) {
+        const A t = (A)K.cs2_rel * lcs2;
+        lv2 += t;
+        lca2 += t;
+        lbt2 += t;
+    } else {
+        lP += (A)K.gamma * Air * lcs2;
+        lir += (A)K.gamma * (A)P * lcs2;
+    }
+    lv[0] += A(2) * Avn * lv2;
+    lv[1] += A(2) * Avt1 * lv2;
+    lv[2] += A(2) * Avt2 * lv2;
+    lbtm += Air * lbt2;
+    lir += (A)btm * lbt2;
+    lBt1 += A(2) * ABt1 * lbtm;
+    lBt2 += A(2) * ABt2 * lbtm;
+    const A lBn = A(2) * (A)Bn * Air * lca2;
+    lir += (A)Bn * (A)Bn * lca2;
+    lr -= Air * (Air * lir);
+    lw[0] = lr;
+    lw[1] = lv[0];
+    lw[2] = lv[1];
+    lw[3] = lv[2];
+    lw[4] = lBn;
+    lw[5] = lBt1;
+    lw[6] = lBt2;
+    lw[7] = lP;
+}
+
 // phi_N(a, b, c, d) of Sec. 2.2 (the weights of the forward step: JS, or
 // WENO-Z with the ratio clamped at 1e18 in float) and its gradient in (a, b,
 // c, d), by hand: smoothness indicators -> weights (through tau for WENO-Z)
@@ -386,7 +839,6 @@ __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq
 // in the float path, whose Jacobians are float).
 template <int AX, typename B, int VAR>
 __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
-    using D8 = Dual<B, 8>;
     using A = typename std::conditional<std::is_same<B, float>::value, float, double>::type;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long n = (long long)nx * ny * nz;
@@ -462,39 +914,38 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
         alpha[mo] = a2 >= a3 ? a2 : a3;
         asign[mo] = (a2 >= a3 ? x2 : x3) >= B(0) ? B(1) : B(-1);
     }
-    // eigenvectors on dual numbers over the interface state
-    D8 wd[8];
+    // eigenvectors at the interface state (values); their dependence on the
+    // state is reversed by eigen7_rev after the mode loop
+    B wv[8];
     const int prim[8] = {C_RHO, C_VN, C_VT1, C_VT2, C_BN, C_BT1, C_BT2, C_P};
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        wd[t] = D8(B(B(0.5) * (Q(prim[t], 2) + Q(prim[t], 3))));
-        wd[t].d[t] = B(1);
-    }
-    D8 Ld[7][7], Rd[7][7];
-    eigen7<D8>(wd, promote<B, 8>(K), Ld, Rd);
+    for (int t = 0; t < 8; ++t) wv[t] = B(0.5) * (Q(prim[t], 2) + Q(prim[t], 3));
+    B Lv[7][7], Rv[7][7];
+    eigen7<B>(wv, K, Lv, Rv);
+    A lLm[7][7], lRm[7][7];
     const B eps4 = B(4) * K.eps_w;
     A lX[11][7];
 #pragma unroll
     for (int x = 0; x < 11; ++x)
 #pragma unroll
         for (int c = 0; c < 7; ++c) lX[x][c] = A(0);
-    A lw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    A lw[8];
     A lalpha[7];
 #pragma unroll 1
     for (int mo = 0; mo < 7; ++mo) {
         B Pm[11];
 #pragma unroll
         for (int x = 0; x < 11; ++x) {
-            B acc = Ld[mo][0].v * X[x][0];
+            B acc = Lv[mo][0] * X[x][0];
 #pragma unroll
-            for (int c = 1; c < 7; ++c) acc = acc + Ld[mo][c].v * X[x][c];
+            for (int c = 1; c < 7; ++c) acc = acc + Lv[mo][c] * X[x][c];
             Pm[x] = acc;
         }
         B phi, gP[11], ga;
         weno_field_grad<B, VAR>(Pm, alpha[mo], eps4, phi, gP, ga);
         A lphi = A(0);
 #pragma unroll
-        for (int c = 0; c < 7; ++c) lphi += (A)Rd[mo][c].v * lFf[c];
+        for (int c = 0; c < 7; ++c) lphi += (A)Rv[mo][c] * lFf[c];
         lalpha[mo] = lphi * (A)ga;
         A lL[7] = {0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -502,17 +953,17 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjSweepArgs<B> a) {
             const A lp = lphi * (A)gP[x];
 #pragma unroll
             for (int c = 0; c < 7; ++c) {
-                lX[x][c] += lp * (A)Ld[mo][c].v;
+                lX[x][c] += lp * (A)Lv[mo][c];
                 lL[c] += lp * (A)X[x][c];
             }
         }
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
-            const A lR = (A)phi * lFf[c];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) lw[t] += lL[c] * (A)Ld[mo][c].d[t] + lR * (A)Rd[mo][c].d[t];
+            lLm[mo][c] = lL[c];
+            lRm[mo][c] = (A)phi * lFf[c];
         }
     }
+    eigen7_rev<B, A>(wv, K, lLm, lRm, lw);
     // adjoints of the cells' quantities
     A lq[6][NCQ];
 #pragma unroll
