@@ -17,7 +17,6 @@
 
 #include <type_traits>
 
-#include "w5ct_dual.cuh"
 #include "w5ct_kernels.cuh"
 
 namespace w5ct {
@@ -213,8 +212,8 @@ __device__ __forceinline__ void speeds_rev(B cs2, B ca2, B bt2, A lfmc, A lcms, 
 // interface state w, written by hand from the forward formulas (recomputed
 // here in B; the adjoints in A).  Branches follow the primal values: the
 // epsilon_B switches and the WENO sign sg, the c_s^2 bound of the float
-// path, the sqrt of zero (subgradient 0) -- the same choices the
-// dual-number form of eigen7 makes.
+// path, the sqrt of zero (subgradient 0): the derivative of the branch the
+// forward step takes.
 template <typename B, typename A>
 __device__ __forceinline__ void eigen7_rev(const B (&w)[8], const Phys<B> &K, const A (&lL)[7][7], const A (&lR)[7][7],
                                            A (&lw)[8]) {
@@ -702,9 +701,9 @@ __device__ __forceinline__ void weno_field_grad(const B (&P)[11], B alpha, B eps
 // Reverse of cell_fill<B, AX>: given the adjoints lq of a cell's 23
 // quantities, the adjoints of its eight inputs (rho, m_x, m_y, m_z, E, B_x,
 // B_y, B_z) in out.  The primitives and the flux are differentiated by hand
-// (Eq. P and Eq. fluxes); the three wave speeds, when their adjoints are not
-// zero (the two cells next to the face), on dual numbers over (rho, P, B_n,
-// B_t1, B_t2).  The floors, when they apply, cut the dependence as in the
+// (Eq. P and Eq. fluxes), and so are the three wave speeds when their
+// adjoints are not zero (the two cells next to the face), through
+// speeds_rev.  The floors, when they apply, cut the dependence as in the
 // forward step.
 template <typename B, typename A, int AX>
 __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq)[NCQ], const Phys<B> &K,
@@ -765,34 +764,38 @@ __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq
     lB1 += lvB * v1 + lPt * b1;
     lB2 += lvB * v2 + lPt * b2;
     lP += lPt;
-    // wave speeds on dual numbers over (r, P, Bn, B1, B2)
+    // wave speeds c_f, c_A, c_slow of the cell from (r, P, Bn, B1, B2),
+    // reversed by hand (Eqs. slow/fast through speeds_rev; |Bn| and sqrt(0)
+    // take the sign of Bn and the subgradient 0)
     const A lcf = lq[C_CF], lca = lq[C_CA], lcs = lq[C_CSL];
     if (lcf != A(0) || lca != A(0) || lcs != A(0)) {
-        using D5 = Dual<B, 5>;
-        using m5 = M<D5>;
-        D5 x[5];
-        const B xv[5] = {r, P, Bn, B1, B2};
-#pragma unroll
-        for (int t = 0; t < 5; ++t) {
-            x[t] = D5(xv[t]);
-            x[t].d[t] = B(1);
-        }
-        const D5 irr = m5::rcp_(x[0]);
-        const D5 cs2 = D5(K.gamma) * x[1] * irr;
-        const D5 ca2 = x[2] * x[2] * irr;
-        const D5 bt2 = (x[3] * x[3] + x[4] * x[4]) * irr;
-        D5 fmc, cms, cf2, csl2;
-        speeds<D5>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
-        const D5 cf = m5::sqrt_(cf2), csl = m5::sqrt_(csl2);
-        const D5 ca = m5::abs_(x[2]) * (m5::sqrt_(x[0]) * irr);
-        A g[5];
-#pragma unroll
-        for (int t = 0; t < 5; ++t) g[t] = lcf * (A)cf.d[t] + lca * (A)ca.d[t] + lcs * (A)csl.d[t];
-        lr += g[0];
-        lP += g[1];
-        lBn += g[2];
-        lB1 += g[3];
-        lB2 += g[4];
+        using mb = M<B>;
+        const B irr = mb::rcp_(r);
+        const B cs2 = K.gamma * P * irr, ca2 = Bn * Bn * irr, bt2 = (B1 * B1 + B2 * B2) * irr;
+        B fmc, cms, cf2, csl2;
+        speeds<B>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
+        const B cf = mb::sqrt_(cf2), csl = mb::sqrt_(csl2), sr = mb::sqrt_(r);
+        const A lcf2 = cf > B(0) ? lcf * A(0.5) / (A)cf : A(0);
+        const A lcsl2 = csl > B(0) ? lcs * A(0.5) / (A)csl : A(0);
+        A lcs2 = A(0), lca2 = A(0), lbt2 = A(0);
+        speeds_rev<B, A>(cs2, ca2, bt2, A(0), A(0), lcf2, lcsl2, lcs2, lca2, lbt2);
+        // c_A = |Bn| (sqrt(r) / r)
+        const A Airr = (A)irr, Asr = (A)sr;
+        const A sgn = Bn >= B(0) ? A(1) : A(-1);
+        lBn += lca * sgn * Asr * Airr;
+        const A lq_ = lca * sgn * (A)Bn;              // adjoint of sqrt(r) / r
+        A lirr = lq_ * Asr;
+        const A lsr = lq_ * Airr;
+        if (sr > B(0)) lr += lsr * A(0.5) / Asr;
+        // cs2 = gamma P / r, ca2 = Bn^2 / r, bt2 = (B1^2 + B2^2) / r
+        lP += (A)K.gamma * Airr * lcs2;
+        lirr += (A)K.gamma * (A)P * lcs2;
+        lBn += A(2) * (A)Bn * Airr * lca2;
+        lirr += (A)Bn * (A)Bn * lca2;
+        lB1 += A(2) * (A)B1 * Airr * lbt2;
+        lB2 += A(2) * (A)B2 * Airr * lbt2;
+        lirr += ((A)B1 * (A)B1 + (A)B2 * (A)B2) * lbt2;
+        lr -= Airr * (Airr * lirr);
     }
     // P = gm1 (E - r vv / 2 - BB / 2)
     if (!pfloor) {
@@ -830,11 +833,9 @@ __device__ __forceinline__ void cell_fill_adjoint(const B (&in)[8], const A (&lq
 // formulas of cell_fill and face_flux), then the transposes of the linear
 // parts (stencil combinations, projection on the left eigenvectors,
 // back-projection on the right ones), of phi_N (phi_n_grad) and of the cell
-// recovery (cell_fill_adjoint), with dual numbers only where the dependence
-// is nonlinear and narrow: the eigenvectors on the eight interface values
-// and the wave speeds of the two central cells.  Branches follow the primal
-// values (the derivative of the branch the forward step takes).  The 48
-// contributions
+// recovery (cell_fill_adjoint) and of the eigenvectors (eigen7_rev), all
+// written by hand.  Branches follow the primal values (the derivative of the
+// branch the forward step takes).  The 48 contributions
 // d(lam . outputs)/d(input) go to cb; adjoints accumulate in double (float
 // in the float path, whose Jacobians are float).
 template <int AX, typename B, int VAR>

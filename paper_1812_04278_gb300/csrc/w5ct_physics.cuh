@@ -47,16 +47,10 @@ struct Phys {
     int floors;
 };
 
-// Arithmetic-type traits: the plain types here; the dual numbers of the
-// adjoint (w5ct_dual.cuh) specialise them.  float_based<Real> selects the
-// float-specific guards of the FP32-bulk arithmetic.
+// float_based<Real> selects the float-specific guards of the FP32-bulk
+// arithmetic.
 template <typename R>
-struct DualTraits {
-    static constexpr bool is_dual = false;
-    using base = R;
-};
-template <typename R>
-constexpr bool float_based = std::is_same<typename DualTraits<R>::base, float>::value;
+constexpr bool float_based = std::is_same<R, float>::value;
 
 // ---------------------------------------------------------------- math helpers
 template <typename Real> struct M;
@@ -199,7 +193,8 @@ __device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) 
             w0 = A0 * inv;
             w2 = A2 * inv;
         }
-    } else if constexpr (std::is_same<Real, float>::value) {
+    } else {
+        static_assert(std::is_same<Real, float>::value, "phi_n takes float or double");
         const float s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
         float a0, a1, a2;
         if constexpr (VAR == 0) {
@@ -216,34 +211,6 @@ __device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) 
             a2 = 3.0f * (1.0f + r2 * r2);
         }
         const float inv = __fdividef(1.0f, a0 + a1 + a2);
-        w0 = a0 * inv;
-        w2 = a2 * inv;
-    } else {
-        // other arithmetic types (the adjoint's dual numbers): the same
-        // weights written with the type's own operations; the float clamp of
-        // the WENO-Z ratio is kept for float-based types
-        using m = M<Real>;
-        const Real s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
-        Real a0, a1, a2;
-        if constexpr (VAR == 0) {
-            a0 = m::rcp_(s0 * s0);
-            a1 = Real(6) * m::rcp_(s1 * s1);
-            a2 = Real(3) * m::rcp_(s2 * s2);
-        } else {
-            // tau / s_k as quotients (no 1/s_k^2 in the derivative: s_k can
-            // be eps_Z alone where a field is uniform)
-            const Real tau = m::abs_(IS0 - IS2);
-            Real r0 = m::div_(tau, s0), r1 = m::div_(tau, s1), r2 = m::div_(tau, s2);
-            if constexpr (float_based<Real>) {
-                r0 = m::min_(r0, Real(1.0e18));
-                r1 = m::min_(r1, Real(1.0e18));
-                r2 = m::min_(r2, Real(1.0e18));
-            }
-            a0 = Real(1) + r0 * r0;
-            a1 = Real(6) * (Real(1) + r1 * r1);
-            a2 = Real(3) * (Real(1) + r2 * r2);
-        }
-        const Real inv = m::rcp_(a0 + a1 + a2);
         w0 = a0 * inv;
         w2 = a2 * inv;
     }
