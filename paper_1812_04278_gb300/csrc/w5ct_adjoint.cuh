@@ -259,7 +259,7 @@ __device__ __forceinline__ void eigen7_rev(const B (&w)[8], const Phys<B> &K, co
     const B bvB = b1 * vt1 + b2 * vt2;
     const B ics2B = m::rcp_(cs2);
     // the rest in the adjoint type
-    const A Ar = (A)r, Avn = (A)vn, Avt1 = (A)vt1, Avt2 = (A)vt2, ABt1 = (A)Bt1, ABt2 = (A)Bt2;
+    const A Avn = (A)vn, Avt1 = (A)vt1, Avt2 = (A)vt2, ABt1 = (A)Bt1, ABt2 = (A)Bt2;
     const A Av2 = (A)v2, Acf = (A)cf, Acsl = (A)csl, Acs = (A)cs, Acf2 = (A)cf2, Acsl2 = (A)csl2, Acs2 = (A)cs2;
     const A Aaf = (A)af, Aas = (A)as, Ab1 = (A)b1, Ab2 = (A)b2, Asr = (A)sr, Aisr = (A)isr, Abv = (A)bvB;
     const A ics2 = (A)ics2B, pre = A(0.5) * ics2, gm1 = (A)K.gm1, g1 = (A)K.g1, g2 = (A)K.g2;
@@ -268,7 +268,6 @@ __device__ __forceinline__ void eigen7_rev(const B (&w)[8], const Phys<B> &K, co
     const A Gs = Aas * Acsl * Avn + Aaf * Acf * sg * Abv;
     const A k1 = -gm1 * Aaf, k2 = -gm1 * Aas;
     const A V[3] = {Avn, Avt1, Avt2};
-    (void)Ar;
     // ---- adjoints
     A lpre = 0, laf = 0, las = 0, lcf = 0, lcsl = 0, lcs = 0, lsr = 0, lisr = 0, lb1 = 0, lb2 = 0;
     A lGf = 0, lGs = 0, lGa = 0, lv2 = 0, lBt1 = 0, lBt2 = 0, lcf2 = 0, lcsl2 = 0, lcs2 = 0, ltau = 0;
