@@ -72,3 +72,16 @@ def test_create_and_destroy_without_device_work(w5):
     with pytest.raises(ValueError):             # buffers shorter than 3 x npatch
         w5.w5ct_init_grid(ctx, (8, 8, 8), (0.1, 0.1, 0.1), npatch=2)
     w5.w5ct_destroy(ctx)
+
+
+def test_batched_entry_points_validate_on_the_host(w5):
+    """The schedule setter, the fused-wait check and the adjoint entry points
+    reject a context without a grid or state before any device work."""
+    ctx = w5.w5ct_create(w5.w5ct_config_default())
+    for call in (lambda: w5.w5ct_set_sweep_schedule(ctx, 2),
+                 lambda: w5.w5ct_fused_wait_check(ctx, 1000),
+                 lambda: w5.w5ct_tile_variant(ctx, 0, 0)):
+        with pytest.raises(w5.W5ctError) as e:
+            call()
+        assert e.value.code in (w5.W5CT_ERR_ARG, w5.W5CT_ERR_STATE)
+    w5.w5ct_destroy(ctx)
