@@ -1,0 +1,101 @@
+"""Oracle pins for the face -> centre field interpolation (Sec. 2.3) and
+the floors (a reading: they act inside primitive recovery only).  CPU only.
+
+* The cell field is (9 (b_{i-1/2} + b_{i+1/2}) - (b_{i-3/2} + b_{i+3/2})) / 16
+  along each face direction: exact for cubic polynomials at the cell
+  centre, fourth order for smooth fields.
+* With floors on, a uniform state whose pressure lies below the floor is a
+  free-stream state all the same (the floors change the primitives the
+  fluxes see, never the conserved state), the floor hits are counted, and
+  the signal speed is the closed-form fast speed at the floored pressure.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_04278_gb300 import inputs
+
+GAMMA = 5.0 / 3.0
+
+
+def cubic(x):
+    return 0.3 - 1.2 * x + 2.5 * x ** 2 - 1.7 * x ** 3
+
+
+def face_fields(shape, fx, fy, fz):
+    """b_x, b_y, b_z on the forward faces, each a function of its own
+    coordinate only (faces at (i + 1) dx, cell centres at (i + 1/2) dx)."""
+    nx, ny, nz = shape
+    xf = (np.arange(nx) + 1.0) / nx
+    yf = (np.arange(ny) + 1.0) / ny
+    zf = (np.arange(nz) + 1.0) / nz
+    o = np.ones((nz, ny, nx))
+    return np.stack([o * fx(xf)[None, None, :], o * fy(yf)[None, :, None], o * fz(zf)[:, None, None]])
+
+
+def centre_field(shape, bface):
+    cons, _ = inputs.uniform_state(shape, rho=1.0, P=1.0)
+    o = oracle.Oracle(shape, tuple(1.0 / n for n in shape))
+    o.set_state(cons, bface)
+    _, _, bcell = o.get_state()
+    o.close()
+    return bcell
+
+
+def test_cell_field_is_exact_for_cubics():
+    shape = (16, 12, 10)
+    bface = face_fields(shape, cubic, lambda y: cubic(1.0 - y), lambda z: cubic(0.5 * z))
+    bc = centre_field(shape, bface)
+    nx, ny, nz = shape
+    xc, yc, zc = (np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny, (np.arange(nz) + 0.5) / nz
+    # interior cells: the four faces i-3/2 .. i+3/2 need no periodic wrap
+    ex = np.abs(bc[0][:, :, 2:nx - 1] - cubic(xc[2:nx - 1])[None, None, :]).max()
+    ey = np.abs(bc[1][:, 2:ny - 1, :] - cubic(1.0 - yc[2:ny - 1])[None, :, None]).max()
+    ez = np.abs(bc[2][2:nz - 1, :, :] - cubic(0.5 * zc[2:nz - 1])[:, None, None]).max()
+    assert max(ex, ey, ez) < 1e-14, (ex, ey, ez)
+    # the wrapped cells see the jump of the non-periodic cubic: not exact
+    assert np.abs(bc[0][:, :, 0] - cubic(xc[0])).max() > 1e-3
+
+
+def test_cell_field_converges_at_fourth_order():
+    errs = []
+    for n in (8, 16, 32):
+        shape = (n, 4, 4)
+        k = 2 * np.pi
+        bface = face_fields(shape, lambda x: np.sin(k * x), lambda y: np.zeros_like(y), lambda z: np.zeros_like(z))
+        bc = centre_field(shape, bface)
+        xc = (np.arange(n) + 0.5) / n
+        errs.append(np.abs(bc[0][0, 0, :] - np.sin(k * xc)).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 3.8), (errs, orders)
+
+
+def fast_speed(rho, P, Bn, Bt2):
+    """c_f from the root formula (reading of Eqs. slow/fast)."""
+    cs2, ca2, bt2 = GAMMA * P / rho, Bn * Bn / rho, Bt2 / rho
+    s = cs2 + ca2 + bt2
+    return np.sqrt(0.5 * (s + np.sqrt(s * s - 4.0 * cs2 * ca2)))
+
+
+def test_floors_touch_only_the_primitives():
+    shape = (8, 6, 4)
+    v, B, P, p_min = (0.3, -0.2, 0.1), (0.5, 0.2, -0.1), 1e-10, 1e-8
+    cons, bface = inputs.uniform_state(shape, rho=1.0, v=v, B=B, P=P)
+    o = oracle.Oracle(shape, tuple(1.0 / n for n in shape),
+                      oracle.make_config(floors=1, rho_min=1e-8, p_min=p_min))
+    o.set_state(cons, bface)
+    S = o.max_signal_speed()
+    for d in range(3):
+        Bt2 = sum(B[e] ** 2 for e in range(3) if e != d)
+        floored = abs(v[d]) + fast_speed(1.0, p_min, B[d], Bt2)
+        raw = abs(v[d]) + fast_speed(1.0, P, B[d], Bt2)
+        assert abs(S[d] - floored) <= 1e-12 * floored, (d, S[d], floored)
+        assert abs(S[d] - raw) > 1e-9 * raw        # the floored pressure, not the stored one
+    dt = o.cfl_dt()
+    o.step(dt)
+    c, b, _ = o.get_state()
+    hits, bad = o.status()
+    o.close()
+    assert bad == 0 and hits > 0
+    assert np.abs(c - cons).max() <= 1e-14 * np.abs(cons).max()
+    assert np.abs(b - bface).max() <= 1e-14 * np.abs(bface).max()
