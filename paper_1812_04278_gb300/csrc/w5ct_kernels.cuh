@@ -259,6 +259,17 @@ struct StageW {
 #ifndef W5CT_UPD_MINB
 #define W5CT_UPD_MINB 1
 #endif
+// Minimum resident blocks per SM of the single-patch stage update.  The float
+// form streams float fluxes and double accumulators (HBM-bound): 4 blocks/SM
+// (64 registers) hide more memory latency than 2 (at 96-115 registers), 2.2%
+// on the 256^3 FP32-bulk step.  The double form is FP64-pipe bound: 1.
+#ifndef W5CT_F32_UPD_MINB
+#define W5CT_F32_UPD_MINB 4
+#endif
+template <typename Real>
+struct UpdTuning {
+    static constexpr int MINB = sizeof(Real) == 4 ? W5CT_F32_UPD_MINB : W5CT_UPD_MINB;
+};
 
 // geometry of the patch an update thread works on
 template <typename Real>
@@ -443,7 +454,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
 }
 
 template <typename Real, int STAGE>
-__global__ void __launch_bounds__(256, W5CT_UPD_MINB) update_kernel(UpdateArgs<Real> a) {
+__global__ void __launch_bounds__(256, UpdTuning<Real>::MINB) update_kernel(UpdateArgs<Real> a) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
     if (i >= a.nx || j >= a.ny) return;
     const UpdGeom<Real> ug = {a.nx, a.ny, a.nz, 0, a.rdx, a.rdy, a.rdz, a.drdx, a.drdy, a.drdz};
