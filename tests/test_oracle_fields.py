@@ -141,3 +141,31 @@ def test_step_commutes_with_reflection(variant):
     S = max(np.abs(ca).max(), np.abs(ba).max())
     assert np.abs(rc - ca).max() <= 1e-14 * S
     assert np.abs(rb - ba).max() <= 1e-14 * S
+
+
+def test_step_commutes_with_density_scaling():
+    """Ideal MHD is invariant under rho, P, E -> 4x and B -> 2x with v
+    unchanged (every wave speed stays the same), and so is the scheme with
+    WENO-Z, whose epsilon_Z = 1e-40 lies below rounding: with factors that
+    are powers of two every operation scales exactly, so the scaled state
+    steps to exactly the scaled result.  A wrong power of rho anywhere (the
+    sqrt(rho) of the Alfven and magnetosonic eigenvectors, the B / sqrt(rho)
+    of c_A) breaks this."""
+    shape = (12, 8, 6)
+    dx = tuple(1.0 / n for n in shape)
+    cons, bface = inputs.random_smooth_state(shape, seed=91)
+    a = oracle.Oracle(shape, dx, oracle.make_config(weno_variant=oracle.WENO_Z))
+    b = oracle.Oracle(shape, dx, oracle.make_config(weno_variant=oracle.WENO_Z))
+    a.set_state(cons, bface)
+    b.set_state(4.0 * cons, 2.0 * bface)
+    dt = a.cfl_dt()
+    assert b.cfl_dt() == dt
+    for _ in range(3):
+        a.step(dt)
+        b.step(dt)
+    ca, ba, _ = a.get_state()
+    cb, bb, _ = b.get_state()
+    a.close()
+    b.close()
+    assert np.array_equal(cb, 4.0 * ca)
+    assert np.array_equal(bb, 2.0 * ba)
