@@ -169,3 +169,30 @@ def test_step_commutes_with_density_scaling():
     b.close()
     assert np.array_equal(cb, 4.0 * ca)
     assert np.array_equal(bb, 2.0 * ba)
+
+
+def test_step_commutes_with_velocity_scaling():
+    """The other unit change of ideal MHD: v, B -> 2x, P, E -> 4x (rho
+    fixed) is the same flow run twice as fast, so the CFL step halves and a
+    step of dt/2 of the scaled state is exactly the scaled step of dt (WENO-Z,
+    powers of two).  Together with the density scaling this pins how dt
+    enters the stages and the relative dimensions of every v, B and P term."""
+    shape = (12, 8, 6)
+    dx = tuple(1.0 / n for n in shape)
+    cons, bface = inputs.random_smooth_state(shape, seed=93)
+    sc = np.array([1.0, 2.0, 2.0, 2.0, 4.0])[:, None, None, None]
+    a = oracle.Oracle(shape, dx, oracle.make_config(weno_variant=oracle.WENO_Z))
+    b = oracle.Oracle(shape, dx, oracle.make_config(weno_variant=oracle.WENO_Z))
+    a.set_state(cons, bface)
+    b.set_state(sc * cons, 2.0 * bface)
+    dt = a.cfl_dt()
+    assert b.cfl_dt() == 0.5 * dt
+    for _ in range(3):
+        a.step(dt)
+        b.step(0.5 * dt)
+    ca, ba, _ = a.get_state()
+    cb, bb, _ = b.get_state()
+    a.close()
+    b.close()
+    assert np.array_equal(cb, sc * ca)
+    assert np.array_equal(bb, 2.0 * ba)
