@@ -112,8 +112,9 @@ int w5ct_init_grid(w5ct_ctx *ctx, int npatch, const int *n3, const double *dx3);
 int w5ct_set_state(w5ct_ctx *ctx, int patch, const double *cons, const double *bface, int on_device);
 
 /* Read the state back; any of cons / bface / bcell may be NULL.  Synchronises.
- * Returns W5CT_ERR_NONPHYSICAL if a step since the last check met a
- * non-physical state (the buffers are still written). */
+ * Returns W5CT_ERR_TIMEOUT if a wait of a fused step (schedule 2) expired
+ * since the last check, and W5CT_ERR_NONPHYSICAL if a step met a non-physical
+ * state (in both cases the buffers are still written). */
 int w5ct_get_state(w5ct_ctx *ctx, int patch, double *cons, double *bface, double *bcell, int on_device);
 
 /* One full RK4 + CT step of size dt > 0 (Secs. 2.1, 2.3, 3.1.3) of every
