@@ -8,7 +8,7 @@ states returned by the solver; not part of a step).
   one Fourier mode of the state; the decay of one wave family, free of the
   small other waves (same wave vector) that the CT update's dispersion
   excites and that make an RMS of B rise and fall.
-* transverse_flux_rms (Sec. 4.3): RMS over the cells of
+* transverse_flux_rms (Sec. 4.2): RMS over the cells of
   sqrt((B_1 v_1)^2 + (B_2 v_2)^2) with 1, 2 the transverse directions of
   the wave frame; the robust dissipation measure of the polarised Alfven
   wave.

@@ -418,7 +418,7 @@ def ic_from_potential(rho, v, P, A, B0, dx, gamma=GAMMA):
 
 def cpaw_overpressure(shape, amp=0.1, kint=(1, 2, 2), p0=0.1, peak=10.0, r0=0.1, rho0=1.0):
     """Primitive fields and edge vector potential of a circularly polarised
-    Alfven wave (Sec. 4.3 set-up: rho = 1, B_par = 1, P = 0.1, v_perp =
+    Alfven wave (Sec. 4.2 set-up: rho = 1, B_par = 1, P = 0.1, v_perp =
     B_perp = amp (sin phi, cos phi) in the wave frame) travelling along
     k = 2 pi kint in the unit box, plus a Gaussian overpressure
     P = p0 (1 + (peak - 1) exp(-r^2 / r0^2)) about the box centre.  The
@@ -448,13 +448,13 @@ def cpaw_overpressure(shape, amp=0.1, kint=(1, 2, 2), p0=0.1, peak=10.0, r0=0.1,
 
 
 # --------------------------------------------------------------------------
-# robustness problems (Secs. 4.4, 4.5, 4.12)
+# robustness problems (Secs. 4.3, 4.5, 4.14)
 # --------------------------------------------------------------------------
 
 
 def field_loop(shape=(128, 64, 1), L=(2.0, 1.0, 1.0), A0=1e-3, rc=0.3, v=(2.0, 1.0, 0.0), rho=1.0, P=1.0,
                gamma=GAMMA):
-    """Magnetic field loop advection (Sec. 4.12): periodic L_x x L_y box,
+    """Magnetic field loop advection (Sec. 4.14): periodic L_x x L_y box,
     uniform rho, v, P, and b = curl (0, 0, A_z) with A_z = A0 (rc - r) for
     r < rc (0 outside) about the box centre, on the edges (i+1/2, j+1/2);
     cell field by the sixth-order interpolation (Sec. 4.14).  Returns
@@ -480,7 +480,7 @@ def magnetic_energy(bface, dx):
 
 # Riemann problems as printed (primitive U = (rho, v_x, v_y, v_z, B_x, B_y, B_z, P)).
 _S4PI = np.sqrt(4.0 * np.pi)
-# Sec. 4.4 prints seven entries for the left state; read as (rho, v_x, v_y,
+# Sec. 4.3 prints seven entries for the left state; read as (rho, v_x, v_y,
 # B_x, B_y, B_z, P) with v_z = 0 (the right state has all eight).
 RJ2A = dict(left=(1.08, 1.2, 0.01, 0.0, 2.0 / _S4PI, 3.6 / _S4PI, 2.0 / _S4PI, 0.95),
             right=(1.0, 0.0, 0.0, 0.0, 2.0 / _S4PI, 4.0 / _S4PI, 2.0 / _S4PI, 1.0), gamma=5.0 / 3.0, t_end=0.2)

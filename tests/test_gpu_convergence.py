@@ -51,7 +51,7 @@ def test_fast_wave_decay_rate_converges_at_high_order(env):
 
 
 def cpaw_return(env, n, periods=1):
-    """The circularly polarised Alfven wave of Sec. 4.3 (rho = 1, P = 0.1,
+    """The circularly polarised Alfven wave of Sec. 4.2 (rho = 1, P = 0.1,
     B_par = 1, amplitude 0.1) along k = 2 pi (1, 2, 2): an exact nonlinear
     solution moving at c_A = 1, back in its initial position after every
     period 1/3.  Returns the L1 distance of the cell-centred field from its
@@ -82,7 +82,7 @@ def test_cpaw_periodic_return(env):
     """After a whole period the wave is back where it started: the L1
     distance of the field from the initial state falls at second order (the
     CT update) and the decay rate of the transverse flux at fifth order (the
-    fifth-order fluxes; Sec. 4.3).  Measured on a GB300: L1 1.58e-3, 6.13e-4,
+    fifth-order fluxes; Sec. 4.2).  Measured on a GB300: L1 1.58e-3, 6.13e-4,
     1.78e-4 and rate 0.183, 5.9e-3, 1.8e-4 at 16^3, 32^3, 64^3."""
     res = {n: cpaw_return(env, n) for n in (16, 32, 64)}
     l1_order = np.log2(res[32][0] / res[64][0])

@@ -1,4 +1,4 @@
-"""Robustness problems through the C ABI (Secs. 4.4, 4.5, 4.11, 4.12).
+"""Robustness problems through the C ABI (Secs. 4.3, 4.5, 4.13, 4.14).
 
 * Riemann problems: FP64 steps equal the oracle's to 1e-12 along the
   trajectory (each step from identical input), including the degenerate
@@ -6,8 +6,8 @@
   Appendix A's beta vectors take their fallback); both forms reach the
   paper's end times without a non-physical state and without floors.
 * Field loop: the GPU keeps the oracle's magnetic-energy history and more
-  than 90% of the energy at 128 x 64 (Sec. 4.12).
-* Square advection (Sec. 4.11): WENO-Z has the smaller L1 error than WENO5,
+  than 90% of the energy at 128 x 64 (Sec. 4.14).
+* Square advection (Sec. 4.13): WENO-Z has the smaller L1 error than WENO5,
   as the paper reports.
 """
 import numpy as np

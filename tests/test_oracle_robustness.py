@@ -1,10 +1,10 @@
-"""Robustness problems on the CPU oracle (Secs. 4.4, 4.5, 4.11, 4.12).
+"""Robustness problems on the CPU oracle (Secs. 4.3, 4.5, 4.13, 4.14).
 
 Pins of the oracle against what the paper reports for them:
-* field loop advection (Sec. 4.12): WENO5 keeps more than 90% of the loop's
+* field loop advection (Sec. 4.14): WENO5 keeps more than 90% of the loop's
   magnetic energy through t = 2 (checked at 128 x 64, where this oracle keeps
   94%; at 64 x 32 it keeps 88.6%, below the paper's figure);
-* Riemann problems (Secs. 4.4, 4.5): no non-physical state without floors to
+* Riemann problems (Secs. 4.3, 4.5): no non-physical state without floors to
   the paper's end times, conservation and div b at round-off, including the
   degenerate transverse field of the Brio-Wu problem.
 """
