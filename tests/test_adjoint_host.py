@@ -14,7 +14,13 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from paper_1812_04278_gb300 import adjoint  # noqa: E402  (needs the built library to import)
+
+@pytest.fixture(scope="module")
+def adjoint():
+    from paper_1812_04278_gb300 import build
+    build.build()                      # the binding imports the library
+    from paper_1812_04278_gb300 import adjoint as mod
+    return mod
 
 
 class FakeSolver:
@@ -67,7 +73,7 @@ def make_fake_w5(dV):
                                  w5ct_adjoint_step=adjoint_step, w5ct_ic_from_potential_adjoint=ic_adjoint)
 
 
-def test_rollout_gradient_matches_central_differences(monkeypatch):
+def test_rollout_gradient_matches_central_differences(monkeypatch, adjoint):
     shape = (4, 3, 2)
     grid = (shape[2], shape[1], shape[0])
     dV = 1.0 / 24
