@@ -144,7 +144,7 @@ int w5ct_step_graph(w5ct_ctx *ctx, int nsteps);
  * paper, whose sweeps run over one patch's pencils).  Each patch is swept
  * along each axis in tiles of BX cells along x times T2 faces or pencils in
  * the second direction, one of these variants:
- *   0: BX = 32, T2 = 16 (FP32_BULK) or 8 (FP64, x-sweep) / 16 (FP64, y, z)
+ *   0: BX = 32, T2 = 16 (FP32_BULK and FP64, every axis)
  *   1: BX = 16, T2 = 16      2: BX = 8, T2 = 16      3: BX = 8, T2 = 8
  * (variants 1-3 in FP32_BULK only).  The variant changes only which threads
  * compute a face, never its arithmetic: results are bit for bit the same.
@@ -290,10 +290,11 @@ const char *w5ct_last_error(const w5ct_ctx *ctx);
 #define W5CT_NOALLOC_MAX_CELLS 134217728LL
 
 /* The reduction of w5ct_conserved_totals for callers that cannot allocate
- * device memory: code running while a CUDA stream is being captured,
- * frameworks that reserve all device memory at start-up and forbid later
- * allocations, and real-time host loops that cannot take the implicit
- * synchronisation of cudaMalloc.  The paper has no counterpart; it is a
+ * device memory: frameworks that reserve all device memory at start-up and
+ * forbid later allocations, and real-time host loops that cannot take the
+ * implicit synchronisation of cudaMalloc.  The call copies the totals to the
+ * host and synchronises its stream, so it cannot be enqueued on a stream
+ * that is being captured.  The paper has no counterpart; it is a
  * convenience of this library.
  *   cons   device pointer, 5 planes of nx*ny*nz doubles (rho, m_x, m_y, m_z, E)
  *   bface  device pointer, 3 planes (b_x, b_y, b_z on the forward faces)
@@ -304,8 +305,10 @@ const char *w5ct_last_error(const w5ct_ctx *ctx);
  * No context is needed and nothing is allocated: the partial sums live in a
  * fixed 512 KB device array inside the library, which every GPU that loads
  * the library holds until the process exits.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the array, so
+ * looks up that array's device address (cudaGetSymbolAddress) and keeps it
+ * for later calls on that device; the kept address is void after the
+ * device is reset (cudaDeviceReset), which this library never does.  All
+ * calls share the array, so
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and must be serialised by the caller.  Errors: W5CT_ERR_ARG for null
  * pointers, sizes < 1, spacings <= 0 or more than W5CT_NOALLOC_MAX_CELLS

@@ -1,6 +1,6 @@
 // w5ct_fused32.cu -- the fused persistent step kernel for Real = float (one
-// translation unit per arithmetic type, compiled with global loads cached in
-// L2 only; see w5ct_fused.cuh).
+// translation unit per arithmetic type, compiled in parallel; see
+// w5ct_fused.cuh).
 #include "w5ct_fused.cuh"
 
 namespace w5ct {

@@ -1,11 +1,12 @@
 // w5ct_noalloc.cu -- w5ct_conserved_totals_noalloc: the conserved-totals
 // reduction of w5ct_conserved_totals, for callers that cannot allocate
-// device memory (code that runs while a CUDA stream is being captured,
-// frameworks that reserve all device memory up front and forbid later
-// cudaMalloc, and real-time host loops that cannot afford the implicit
-// synchronisation of an allocation).  It takes the caller's device arrays
-// directly, needs no context, and keeps its scratch -- one partial record
-// per block and the final record -- in a fixed array in this file.
+// device memory (frameworks that reserve all device memory up front and
+// forbid later cudaMalloc, and real-time host loops that cannot afford the
+// implicit synchronisation of an allocation).  It takes the caller's device
+// arrays directly, needs no context, and keeps its scratch -- one partial
+// record per block and the final record -- in a fixed array in this file.
+// It ends by copying the totals to the host and synchronising the stream,
+// so it is not meant for a stream under capture.
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -30,6 +31,7 @@ static __device__ __align__(256) double g_totals_scratch[(kNaMaxBlocks + 1) * kN
 namespace {
 
 // device address of g_totals_scratch per device, looked up once per device
+// (void after a cudaDeviceReset of that device, which the library never does)
 std::mutex g_mu;
 double *g_scratch_ptr[256] = {nullptr};
 

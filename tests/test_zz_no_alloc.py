@@ -1,9 +1,14 @@
 """w5ct_conserved_totals_noalloc: the conserved-totals reduction for callers
-that cannot allocate device memory (stream capture, frameworks that own all
-device memory, real-time loops).  Checked through the C ABI against the
-regular entry point w5ct_conserved_totals on two calls in a row with
-different inputs, so a second call cannot pass on the first call's leftovers
-in the shared fixed scratch.  This file is collected last on purpose."""
+that cannot allocate device memory (frameworks that own all device memory,
+real-time loops that cannot take an allocation's synchronisation).  Checked
+through the C ABI against the regular entry point w5ct_conserved_totals on
+two calls in a row with different inputs, so a second call cannot pass on
+the first call's leftovers in the shared fixed scratch; and the device's
+free memory is the same before and after a call.
+
+The file name sorts last so that pytest collects it after every other test:
+a run that stops at the first failure (-x) has then already run the rest of
+the suite if this one fails.  Nothing in it depends on the other tests."""
 import numpy as np
 import pytest
 
@@ -34,6 +39,14 @@ def test_noalloc_totals_match_the_context_entry_point(env):
         s.set_state(cons_d, bface_d)
         ref = W.w5ct_conserved_totals(s.ctx)
         got = W.w5ct_conserved_totals_noalloc(cons_d, bface_d, shape, dx, stream)
+        # the first call may load the library's device code lazily; after
+        # it, a call must leave the device's free memory unchanged
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        again = W.w5ct_conserved_totals_noalloc(cons_d, bface_d, shape, dx, stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert np.array_equal(again, got)        # fixed summation order
         absint = np.array([np.abs(cons[f]).sum() for f in range(5)] + [np.abs(bface[f]).sum() for f in range(3)])
         absint *= dx[0] * dx[1] * dx[2]
         assert np.all(np.abs(got - ref) <= 1e-13 * absint), (seed, got - ref)
