@@ -17,8 +17,8 @@ steps at the same dt sequence.
 
 With N > 1 (torchrun) every rank advances its own independent replica
 ("replicas only": the path has no data exchange) and the slowest rank's time
-is used.  --impl reference times the CPU oracle on the host cores on a
-bounded 64^3 sample of the same workload.
+is used.  --impl reference times the CPU oracle on the host cores on the
+same 256^3 workload (K whole steps, about 10 s each on 16 cores).
 """
 from __future__ import annotations
 
@@ -36,17 +36,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic flop counts, obtained by running the oracle's own source with a
-# counting scalar type (+, -, *, / and sqrt count 1; comparisons, max and
-# |x| count 0): per interface of one sweep (interface average, Appendix A
-# eigensystem, 6-point projection of F and q onto 7 fields, LF split and
-# two phi_N per field, back-projection, CT transport fluxes), per cell of
-# one sweep (primitives, flux, three speeds) and per zone-update of the
-# whole RK4 + CT step.  WENO-Z (the benchmarked variant).
-FACE_FLOPS = 2858
+# Algorithmic flop counts per WENO variant (0 = JS, 1 = Z), from the
+# oracle's own source compiled with a counting scalar type
+# (oracle/flopcount.cpp; +, -, *, / and sqrt count 1; negation,
+# comparisons, max and |x| count 0; tests/test_flop_count.py rebuilds the
+# counter and checks these numbers): per cell of one sweep (primitives,
+# flux, three speeds), per interface of one sweep (interface average,
+# Appendix A eigensystem, 6-point projection of F and q onto 7 fields, LF
+# split and two phi_N per field, back-projection), the two CT transport
+# fluxes that the sweep kernel forms at each interface (Eqs. fct1-fct6), and
+# per zone-update of the whole RK4 + CT step.
 CELL_FLOPS = 93
-SWEEP_FLOPS_PER_ZONE = FACE_FLOPS + CELL_FLOPS
-STEP_FLOPS_PER_ZONE = 36057
+FACE_FLOPS = {0: 2760, 1: 2858}
+CT_FLUX_FLOPS = 10
+SWEEP_FLOPS_PER_ZONE = {v: CELL_FLOPS + FACE_FLOPS[v] + CT_FLUX_FLOPS for v in (0, 1)}
+STEP_FLOPS_PER_ZONE = {0: 34881, 1: 36057}
 # Peaks: FP32 from the unit counts (152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz);
 # FP64 from the published GB300 rate (1.25 TFLOP/s); measured copy bandwidth.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -71,7 +75,7 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--ref-n", type=int, default=64, help="edge of the oracle's sample box (reference arm)")
+    p.add_argument("--cpu-steps", type=int, default=2, help="oracle steps of the cpu_baseline leg")
     p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave", "batched", "adjoint"],
                    help="turb: 256^3 turbulence, 50 steps (default); blast: 512^3 blast in Mach-5 turbulence, "
                         "100 steps; wave: the 32^3 fast eigenmode, 20 steps; batched: 512 uneven patches, "
@@ -105,8 +109,11 @@ def workload_config(n):
 
 
 def make_ic(n):
+    """The workload's initial state (2 <= |k| <= 32 at 256^3; boxes too small
+    to hold |k| = 32 keep the modes below their Nyquist wavenumber)."""
     from paper_1812_04278_gb300 import inputs
-    return inputs.turbulent_state(n, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1, kmin=2, kmax=32)
+    return inputs.turbulent_state(n, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1, kmin=2,
+                                  kmax=min(32, n // 2 - 1))
 
 
 # ------------------------------------------------------------------ clocks
@@ -245,36 +252,50 @@ def dist_setup(args):
 # ------------------------------------------------------------------ reference arm
 
 
+def oracle_timed_steps(oracle, o, nsteps):
+    """Seconds of each of nsteps oracle steps, dt from the oracle's own CFL
+    reduction (timed with the step, as on the GPU)."""
+    times = []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        o.step(o.cfl_dt())
+        times.append(time.perf_counter() - t0)
+    return times
+
+
 def run_reference(args):
+    """The oracle, as it stands, on the host cores, on the workload the line
+    names: the full n^3 turbulence box (the same initial state as the native
+    arm), `steps` whole RK4 + CT steps timed.  Warm-up on the CPU only pages
+    memory in, so one untimed step is run instead of `warmup` (the line says
+    so); at about 10 s per 256^3 step on 16 cores the run takes ~4 minutes."""
     world, rank, local, dist = dist_setup(args)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     import oracle
-    from paper_1812_04278_gb300 import inputs
     oracle.build()
-    ns = args.ref_n
-    cons, bface = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
-                                         kmin=2, kmax=min(32, ns // 2 - 1))
-    o = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
+    n = args.n
+    cons, bface = make_ic(n)
+    o = oracle.Oracle((n, n, n), 1.0 / n, oracle.make_config(weno_variant=oracle.WENO_Z))
     o.set_state(cons, bface)
-    for _ in range(args.warmup):
-        o.step(o.cfl_dt())
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(o.cfl_dt())
-    el = time.perf_counter() - t0
-    value = ns ** 3 * args.steps / el
+    warm = 1 if args.warmup > 0 else 0
+    oracle_timed_steps(oracle, o, warm)
+    times = oracle_timed_steps(oracle, o, args.steps)
+    el = sum(times)
+    value = n ** 3 * args.steps / el
     cores = oracle.num_threads()
     line = {
         "impl": "reference", "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value,
-        "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * el / args.steps * (args.n / ns) ** 3, "higher_is_better": True,
+        "unit": "zone-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": warm,
+        "warmup_requested": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.n),
+        "config": workload_config(n),
         "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{ns}^3 box of the same turbulence generator, {args.steps} full steps"},
+                         "sample": f"the {n}^3 workload itself, {args.steps} full steps after {warm} untimed",
+                         "step_seconds_min_max": [min(times), max(times)], "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -413,7 +434,7 @@ def run_native(args):
     peaks = load_peaks()
     value64 = replica_throughput(world, zones, args.steps, ms64)
     value32 = replica_throughput(world, zones, args.steps, ms32)
-    sweep_flops = SWEEP_FLOPS_PER_ZONE * zones
+    sweep_flops = SWEEP_FLOPS_PER_ZONE[1] * zones
     ach64 = sweep_flops / (swms64 / nsw64 * 1e-3) / 1e12
     ach32 = sweep_flops / (swms32 / nsw32 * 1e-3) / 1e12
     line = {
@@ -436,7 +457,7 @@ def run_native(args):
                      "algorithmic_flops_per_launch": sweep_flops,
                      "hbm_gbs": hbm_gbs(sweep_traffic("fp64", zones), swms64 / nsw64),
                      "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "step_tflops": STEP_FLOPS_PER_ZONE * value64 / world / 1e12,
+                     "step_tflops": STEP_FLOPS_PER_ZONE[1] * value64 / world / 1e12,
                      "peak_source": "GB300 FP64 unit count: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz = 1.26; "
                                     "published 1.25 TFLOP/s (probe measured 1.0 TFLOP/s DFMA)"},
         "fp32_bulk": {
@@ -449,7 +470,7 @@ def run_native(args):
                          "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach32 / PEAK_FP32_TFLOPS,
                          "traffic": sweep_traffic("fp32", zones), "launch_ms": swms32 / nsw32,
                          "hbm_gbs": hbm_gbs(sweep_traffic("fp32", zones), swms32 / nsw32),
-                         "step_tflops": STEP_FLOPS_PER_ZONE * value32 / world / 1e12,
+                         "step_tflops": STEP_FLOPS_PER_ZONE[1] * value32 / world / 1e12,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "gpu_launches": launches32,
         },
@@ -468,9 +489,10 @@ def run_native(args):
         "kernel_src": kernel_source_hash(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
-    print(json.dumps(line))
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, cons, bface)
+    if rank == 0:
+        print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 
@@ -494,42 +516,41 @@ def cpu_model() -> str:
         return platform.machine()
 
 
-def cpu_baseline(args):
-    """The oracle, as it stands, on the host cores: full steps on a 64^3
-    sample of the same workload until about args.cpu_seconds have passed."""
+def cpu_baseline(args, cons, bface):
+    """The oracle, as it stands, on the host cores: args.cpu_steps whole
+    steps of the n^3 workload itself (the native arm's initial state), and
+    for the single-core figure a bounded 64^3 box of the same generator for
+    about a quarter of args.cpu_seconds."""
     import oracle
     from paper_1812_04278_gb300 import inputs
     oracle.build()
-    ns = 64
-    cons, bface = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
-                                         kmin=2, kmax=min(32, ns // 2 - 1))
-    o = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
+    n = args.n
+    o = oracle.Oracle((n, n, n), 1.0 / n, oracle.make_config(weno_variant=oracle.WENO_Z))
     o.set_state(cons, bface)
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        o.step(o.cfl_dt())
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= args.cpu_seconds:
-            break
+    times = oracle_timed_steps(oracle, o, args.cpu_steps)
+    el = sum(times)
     cores = oracle.num_threads()
-    value = ns ** 3 * steps / el
-    # the same sample on one core, for about a quarter of the time
+    value = n ** 3 * args.cpu_steps / el
+    o.close()
+    ns = 64
+    c64, b64 = inputs.turbulent_state(ns, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1,
+                                      kmin=2, kmax=min(32, ns // 2 - 1))
     oracle.set_num_threads(1)
-    o.set_state(cons, bface)
+    o1 = oracle.Oracle((ns, ns, ns), 1.0 / ns, oracle.make_config(weno_variant=oracle.WENO_Z))
+    o1.set_state(c64, b64)
     steps1 = 0
     t0 = time.perf_counter()
     while True:
-        o.step(o.cfl_dt())
+        o1.step(o1.cfl_dt())
         steps1 += 1
         el1 = time.perf_counter() - t0
         if el1 >= 0.25 * args.cpu_seconds:
             break
     oracle.set_num_threads(cores)
     return {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full steps of a {ns}^3 box of the same turbulence generator",
-            "seconds": el, "single_core_value": ns ** 3 * steps1 / el1, "single_core_steps": steps1,
+            "sample": f"{args.cpu_steps} full steps of the {n}^3 workload itself", "seconds": el,
+            "single_core_value": ns ** 3 * steps1 / el1,
+            "single_core_sample": f"{steps1} full steps of a {ns}^3 box of the same generator on 1 core",
             "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
@@ -574,7 +595,7 @@ def run_blast(args):
     c32, b32, _ = f.get_state()
     f.close()
     value = zones * args.steps / (ms32 * 1e-3)
-    ach = SWEEP_FLOPS_PER_ZONE * zones / (swms / nsw * 1e-3) / 1e12
+    ach = SWEEP_FLOPS_PER_ZONE[0] * zones / (swms / nsw * 1e-3) / 1e12
     line = {
         "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value, "unit": "zone-updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
@@ -797,7 +818,7 @@ def run_batched(args):
         sv.close()
 
     value = zones * args.steps / (ms32 * 1e-3)
-    ach = SWEEP_FLOPS_PER_ZONE * zones / (swms / nsw * 1e-3) / 1e12
+    ach = SWEEP_FLOPS_PER_ZONE[1] * zones / (swms / nsw * 1e-3) / 1e12
     sizes = np.array([np.prod(sh) for sh in shapes])
     line = {
         "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)", "value": value, "unit": "zone-updates/s",
@@ -814,7 +835,7 @@ def run_batched(args):
         "roofline": {"kernel": "sweep_batched_kernel (FP32)", "bound": "alu", "achieved": ach,
                      "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s", "frac": ach / PEAK_FP32_TFLOPS,
                      "traffic": None, "launch_ms": swms / nsw, "algorithmic_flops_per_launch":
-                     SWEEP_FLOPS_PER_ZONE * zones, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     SWEEP_FLOPS_PER_ZONE[1] * zones, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "fp64_batched": {"value": zones * ne / (ms64 * 1e-3), "ms_per_step": ms64 / ne, "steps": ne,
                          "div_b_linf": divb64},
         "l1_fp32_vs_fp64": {"mean": float(np.mean(l1s)), "max": float(np.max(l1s)), "steps": ne,

@@ -103,6 +103,36 @@ def test_fp64_batch_matches_oracle(env, variant):
     b.close()
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp64_persistent_and_fused_schedules_match_oracle(env, schedule, variant):
+    """Schedules 1 (persistent sweeps) and 2 (the whole step in one persistent
+    launch) against the oracle directly: every patch, after each of two steps
+    of the oracle's own CFL dt, within 1e-12 per step of the state scale."""
+    O, torch = env["O"], env["torch"]
+    sts = states(env, SHAPES, 1300 + 10 * schedule + variant)
+    b = make_batch(env, SHAPES, sts, 0, variant)
+    b.set_schedule(schedule)
+    assert b.schedule() == schedule
+    oras = []
+    for p, sh in enumerate(SHAPES):
+        o = O.Oracle(sh, tuple(1.0 / n for n in sh), O.make_config(weno_variant=variant))
+        o.set_state(*sts[p])
+        oras.append(o)
+    for k in range(2):
+        dts = [o.cfl_dt() for o in oras]
+        b.step_dev(torch.tensor(dts, dtype=torch.float64, device="cuda"))
+        for p, o in enumerate(oras):
+            o.step(dts[p])
+            gc, gb, _ = b.get_state(p)
+            oc, ob, _ = o.get_state()
+            S = max(np.abs(oc).max(), np.abs(ob).max())
+            err = max(np.abs(gc - oc).max(), np.abs(gb - ob).max()) / S
+            assert err <= TOL64 * (k + 1), (k, p, SHAPES[p], err)
+    assert b.status()[1] == 0
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_per_patch_cfl_dt(env, precision):
     """step_cfl gives every patch the dt its own state fixes (Eq. cfl), equal

@@ -43,7 +43,7 @@ def _reference_worker(rank, world, port, q):
     import bench
     buf = io.StringIO()
     with redirect_stdout(buf):
-        bench.main(["--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "0", "--ref-n", "12"])
+        bench.main(["--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "1", "--n", "12"])
     q.put((rank, buf.getvalue()))
 
 
@@ -78,3 +78,5 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["unit"] == "zone-updates/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the oracle ran the workload the line names: its box, the steps it prints
+    assert line["config"]["zones"] == 12 ** 3 and line["steps"] == 1 and line["warmup"] == 1
