@@ -287,10 +287,16 @@ struct UpdGeom {
 // subnormals, infinities and NaNs take the hardware conversion.  A
 // conversion that involves double issues to the FP64 pipe, which the
 // FP32-bulk stage update keeps busy with its accumulations.
+// The hardware conversions of the rare cases sit in functions that are not
+// inlined, so that the compiler branches around them instead of issuing
+// them, predicated off, on the FP64 pipe for every value.
+static __device__ __noinline__ double f2d_special(float x) { return (double)x; }
+static __device__ __noinline__ float d2f_special(double x) { return (float)x; }
+
 __device__ __forceinline__ double f2d_exact(float x) {
     const unsigned u = __float_as_uint(x);
     const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)x;
+    if (e == 0u || e == 0xffu) return f2d_special(x);
     const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
     return __hiloint2double((int)hi, (int)(u << 29));
 }
@@ -298,7 +304,7 @@ __device__ __forceinline__ double f2d_exact(float x) {
 __device__ __forceinline__ float d2f_rn(double x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const int fe = (int)((u >> 52) & 0x7ffu) - 896;          // binary32 exponent field
-    if (fe < 1 || fe > 254) return (float)x;
+    if (fe < 1 || fe > 254) return d2f_special(x);
     const unsigned long long m = u & 0xfffffffffffffULL;
     const unsigned mant = (unsigned)(m >> 29);
     const unsigned long long rem = m & 0x1fffffffULL, half = 1ULL << 28;
