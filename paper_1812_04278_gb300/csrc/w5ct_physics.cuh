@@ -162,72 +162,72 @@ __device__ __forceinline__ Real signal_speed(Real r, Real vn, Real P, Real Bn, R
 
 // ---------------------------------------------------------------- WENO
 // phi_N(a, b, c, d) of Sec. 2.2 with JS (VAR = 0) or WENO-Z (VAR = 1)
-// weights.  The weights are normalised by one division: in double the
-// common denominator of the three alpha_k; in float the alpha_k themselves
-// (reciprocals never overflow there, the WENO-Z ratio is clamped at 1e18).
-template <typename Real, int VAR>
-__device__ __forceinline__ Real phi_n(Real a, Real b, Real c, Real d, Real eps) {
+// weights, in the form the kernels evaluate.
+//
+// Two rewrites that leave phi_N unchanged up to rounding:
+// * the weights depend only on the ratios of eps + IS_k (JS: alpha_k =
+//   d_k / (eps + IS_k)^2 normalised; WENO-Z: tau_5 / (eps + IS_k)), so the
+//   smoothness indicators are evaluated as IS_k / 3 = (13/3) x^2 + y^2 with
+//   eps / 3 (the caller passes it);
+// * with w_k = a_k / D (D = a_0 + a_1 + a_2),
+//   phi_N = w_0 (a - 2b + c)/3 + (w_2 - 1/2)(b - 2c + d)/6
+//         = [a_0 (a - 2b + c) + (a_2 - D/2)((b + d)/2 - c)] / (3 D);
+//   in double each interpolant returns that numerator and D, and weno_field
+//   divides once for the two; in float the weights are normalised first
+//   (D = 1) and phi_N = Nn / 3.
+template <typename Real>
+__device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real &I0, Real &I1, Real &I2) {
+    const Real k = Real(13.0 / 3.0);
     const Real x0 = a - b, x1 = a - Real(3) * b;
-    const Real IS0 = Real(13) * x0 * x0 + Real(3) * x1 * x1;
+    I0 = (k * x0) * x0 + x1 * x1;
     const Real y0 = b - c, y1 = b + c;
-    const Real IS1 = Real(13) * y0 * y0 + Real(3) * y1 * y1;
+    I1 = (k * y0) * y0 + y1 * y1;
     const Real z0 = c - d, z1 = Real(3) * c - d;
-    const Real IS2 = Real(13) * z0 * z0 + Real(3) * z1 * z1;
-    Real w0, w2;
-    if constexpr (std::is_same<Real, double>::value) {
-        const double s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
-        if constexpr (VAR == 0) {
-            const double p0 = s1 * s2, p1 = s0 * s2, p2 = s0 * s1;
-            const double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
-            const double inv = 1.0 / (q0 + 6.0 * q1 + 3.0 * q2);
-            w0 = q0 * inv;
-            w2 = 3.0 * q2 * inv;
-        } else {
-            const double tau = fabs(IS0 - IS2);
-            const double tt = tau * tau;
-            const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
-            const double A0 = (e0 + tt) * (e1 * e2);
-            const double A1 = 6.0 * (e1 + tt) * (e0 * e2);
-            const double A2 = 3.0 * (e2 + tt) * (e0 * e1);
-            const double inv = 1.0 / (A0 + A1 + A2);
-            w0 = A0 * inv;
-            w2 = A2 * inv;
-        }
-    } else {
-        static_assert(std::is_same<Real, float>::value, "phi_n takes float or double");
-        const float s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
-        float a0, a1, a2;
-        if constexpr (VAR == 0) {
-            a0 = __fdividef(1.0f, s0 * s0);
-            a1 = __fdividef(6.0f, s1 * s1);
-            a2 = __fdividef(3.0f, s2 * s2);
-        } else {
-            const float tau = fabsf(IS0 - IS2);
-            const float r0 = fminf(tau * __fdividef(1.0f, s0), 1.0e18f);
-            const float r1 = fminf(tau * __fdividef(1.0f, s1), 1.0e18f);
-            const float r2 = fminf(tau * __fdividef(1.0f, s2), 1.0e18f);
-            a0 = 1.0f + r0 * r0;
-            a1 = 6.0f * (1.0f + r1 * r1);
-            a2 = 3.0f * (1.0f + r2 * r2);
-        }
-        const float inv = __fdividef(1.0f, a0 + a1 + a2);
-        w0 = a0 * inv;
-        w2 = a2 * inv;
-    }
-    return w0 * Real(1.0 / 3.0) * (a - Real(2) * b + c) + (w2 - Real(0.5)) * Real(1.0 / 6.0) * (b - Real(2) * c + d);
+    I2 = (k * z0) * z0 + z1 * z1;
 }
 
-// double: phi_N = Nn / Dn with the weights' common denominator Dn, so that
-// the two interpolants of one field can share a single division.
+// numerator [a_0 (a - 2b + c) + (a_2 - D/2)((b + d)/2 - c)] of phi_N
+template <typename Real>
+__device__ __forceinline__ Real phi_numerator(Real a, Real b, Real c, Real d, Real a0, Real a2, Real D) {
+    const Real t1 = (a - Real(2) * b) + c;
+    const Real t2h = Real(0.5) * (b + d) - c;
+    return a0 * t1 + (a2 - Real(0.5) * D) * t2h;
+}
+
+// float: phi_N = Nn / 3 with the weights normalised here by one reciprocal
+// (the WENO-Z ratio tau_5 / (eps + IS_k) is clamped at 1e18, so nothing
+// overflows; unnormalised WENO-Z weights reach 1e36 in float)
 template <int VAR>
-__device__ __forceinline__ void phi_nd(double a, double b, double c, double d, double eps, double &Nn, double &Dn) {
-    const double x0 = a - b, x1 = a - 3.0 * b;
-    const double IS0 = 13.0 * x0 * x0 + 3.0 * x1 * x1;
-    const double y0 = b - c, y1 = b + c;
-    const double IS1 = 13.0 * y0 * y0 + 3.0 * y1 * y1;
-    const double z0 = c - d, z1 = 3.0 * c - d;
-    const double IS2 = 13.0 * z0 * z0 + 3.0 * z1 * z1;
-    const double s0 = eps + IS0, s1 = eps + IS1, s2 = eps + IS2;
+__device__ __forceinline__ float phi_nf(float a, float b, float c, float d, float eps3) {
+    float I0, I1, I2;
+    smoothness3<float>(a, b, c, d, I0, I1, I2);
+    const float s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
+    float a0, a1, a2;
+    if constexpr (VAR == 0) {
+        a0 = __fdividef(1.0f, s0 * s0);
+        a1 = 6.0f * __fdividef(1.0f, s1 * s1);
+        a2 = 3.0f * __fdividef(1.0f, s2 * s2);
+    } else {
+        const float tau = fabsf(I0 - I2);
+        const float r0 = fminf(tau * __fdividef(1.0f, s0), 1.0e18f);
+        const float r1 = fminf(tau * __fdividef(1.0f, s1), 1.0e18f);
+        const float r2 = fminf(tau * __fdividef(1.0f, s2), 1.0e18f);
+        a0 = 1.0f + r0 * r0;
+        a1 = 6.0f * (1.0f + r1 * r1);
+        a2 = 3.0f * (1.0f + r2 * r2);
+    }
+    const float inv = __fdividef(1.0f, (a0 + a1) + a2);
+    return phi_numerator<float>(a, b, c, d, a0 * inv, a2 * inv, 1.0f);
+}
+
+// double: the weights times the common factor (s_0 s_1 s_2)^2, so that no
+// weight needs a division; phi_N = Nn / (3 D), and the two interpolants of
+// one field share a single division in weno_field.
+template <int VAR>
+__device__ __forceinline__ void phi_nd(double a, double b, double c, double d, double eps3, double &Nn, double &Dn) {
+    double I0, I1, I2;
+    smoothness3<double>(a, b, c, d, I0, I1, I2);
+    const double s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
     double W0, W2;
     if constexpr (VAR == 0) {
         // alpha_k = d_k / s_k^2 times (s0 s1 s2)^2
@@ -237,16 +237,14 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
         Dn = W0 + 6.0 * (p1 * p1) + W2;
     } else {
         // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2
-        const double tau = fabs(IS0 - IS2);
+        const double tau = fabs(I0 - I2);
         const double tt = tau * tau;
         const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
         W0 = (e0 + tt) * (e1 * e2);
         W2 = 3.0 * (e2 + tt) * (e0 * e1);
         Dn = W0 + 6.0 * (e1 + tt) * (e0 * e2) + W2;
     }
-    // phi = w0 (a - 2b + c)/3 + (w2 - 1/2)(b - 2c + d)/6 with w = W / Dn
-    const double t1 = a - 2.0 * b + c, t2 = b - 2.0 * c + d;
-    Nn = (1.0 / 3.0) * W0 * t1 + ((1.0 / 6.0) * W2 - (1.0 / 12.0) * Dn) * t2;
+    Nn = phi_numerator<double>(a, b, c, d, W0, W2, Dn);
 }
 
 // Eq. (FWENO) for one characteristic field from its 11 projections:
@@ -254,10 +252,11 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
 //
 // The split differences are (dF +- alpha dq)/2.  IS_k scales with the square
 // of its arguments and phi_N linearly, so phi_N(x/2; eps) = phi_N(x; 4 eps)/2
-// for both weight variants: the factor 1/2 is applied once to the result and
-// eps4 = 4 eps is passed in.
+// for both weight variants: the factor 1/2 is applied once to the result.
+// With the IS_k / 3 form above the epsilon passed in is eps43 = 4 eps / 3,
+// and F = P[0] + (phi_N^- - phi_N^+)/2 = P[0] + (Nm/Dm - Np/Dp)/6.
 template <typename Real, int VAR>
-__device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps4) {
+__device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps43) {
     Real p[5], q[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
@@ -266,17 +265,19 @@ __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real ep
     }
     if constexpr (std::is_same<Real, double>::value) {
         double Np, Dp, Nm, Dm;
-        phi_nd<VAR>(p[0], p[1], p[2], p[3], eps4, Np, Dp);
-        phi_nd<VAR>(q[4], q[3], q[2], q[1], eps4, Nm, Dm);
+        phi_nd<VAR>(p[0], p[1], p[2], p[3], eps43, Np, Dp);
+        phi_nd<VAR>(q[4], q[3], q[2], q[1], eps43, Nm, Dm);
         const double prod = Dp * Dm;
         if (prod > 1e-290 && prod < 1e290) {
             // -Np/Dp + Nm/Dm over the common denominator: one division
-            return P[0] + 0.5 * ((Nm * Dp - Np * Dm) / prod);
+            return P[0] + (1.0 / 6.0) * ((Nm * Dp - Np * Dm) / prod);
         }
-        return P[0] + 0.5 * (Nm / Dm - Np / Dp);
+        return P[0] + (1.0 / 6.0) * (Nm / Dm - Np / Dp);
     } else {
-        return P[0] + Real(0.5) * (phi_n<Real, VAR>(q[4], q[3], q[2], q[1], eps4) -
-                                   phi_n<Real, VAR>(p[0], p[1], p[2], p[3], eps4));
+        static_assert(std::is_same<Real, float>::value, "weno_field takes float or double");
+        const float Np = phi_nf<VAR>(p[0], p[1], p[2], p[3], eps43);
+        const float Nm = phi_nf<VAR>(q[4], q[3], q[2], q[1], eps43);
+        return __fmaf_rn(1.0f / 6.0f, Nm - Np, P[0]);
     }
 }
 
@@ -512,7 +513,7 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     const Real ics2 = m::rcp_(cs2);
     const Real pre = Real(0.5) * ics2;
     const Real tau = K.gm1 * ics2;
-    const Real eps = Real(4) * K.eps_w;   // see weno_field
+    const Real eps = Real(4.0 / 3.0) * K.eps_w;   // 4 eps / 3: see weno_field
 
     // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
     {
