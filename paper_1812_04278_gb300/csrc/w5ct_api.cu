@@ -60,6 +60,7 @@ struct w5ct_ctx {
     int4 *tiles_buf = nullptr;
     int seg_off[3][kMaxTileVariants] = {};
     int seg_n[3][kMaxTileVariants] = {};
+    int sweep_t2[3] = {0, 0, 0};     // single patch: tile height of the sweep along each axis
     int schedule = 0;                // batched sweeps: 0 = one launch per axis and variant, 1 = persistent,
                                      // 2 = the whole step in one persistent launch (fused)
     // fused step (schedule 2): work items, per-patch targets and counters in one allocation
@@ -608,7 +609,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
                 for (int f = 0; f < 2; ++f) a.S[f] = plane<Real>(Sax[ax], n, f);
                 int rc = record_event(c);
                 if (rc) return rc;
-                W5_CUDA(c, launch_sweep<Real>(ax, variant, a, c->stream));
+                W5_CUDA(c, launch_sweep<Real>(ax, variant, c->sweep_t2[ax], a, c->stream));
                 c->launches++;
                 rc = record_event(c);
                 if (rc) return rc;
@@ -836,6 +837,14 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
         if (rc) return rc;
     }
     W5_CUDA(c, c->cfg.precision == W5CT_FP64 ? prepare_sweeps<double>() : prepare_sweeps<float>());
+    {
+        int dev = 0, sms = 0;
+        W5_CUDA(c, cudaGetDevice(&dev));
+        W5_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        for (int ax = 0; ax < 3; ++ax)
+            c->sweep_t2[ax] = c->cfg.precision == W5CT_FP64 ? choose_sweep_t2<double>(ax, c->nx, c->ny, c->nz, sms)
+                                                            : choose_sweep_t2<float>(ax, c->nx, c->ny, c->nz, sms);
+    }
     c->schedule = 0;
     for (int v = 0; v < n_variants(c); ++v) {
         const cudaError_t eg = c->cfg.precision == W5CT_FP64 ? persistent_grid<double>(c->cfg.weno_variant, v, c->pgrid[v])

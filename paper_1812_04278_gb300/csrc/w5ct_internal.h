@@ -10,9 +10,12 @@ namespace w5ct {
 void set_global_error(const char *text);
 
 // Launch the characteristic sweep along `axis` (0, 1, 2) with WENO variant
-// `variant` (0 = JS, 1 = Z).  Defined in w5ct_sweep32.cu / w5ct_sweep64.cu.
+// `variant` (0 = JS, 1 = Z) over one patch, in tiles `t2` faces or pencils
+// high (0: the type's default, SweepTuning; the FP64 sweep also takes the
+// shorter tiles of small_tile_heights).  Defined in w5ct_sweep32.cu /
+// w5ct_sweep64.cu.
 template <typename Real>
-cudaError_t launch_sweep(int axis, int variant, const SweepArgs<Real> &a, cudaStream_t s);
+cudaError_t launch_sweep(int axis, int variant, int t2, const SweepArgs<Real> &a, cudaStream_t s);
 
 // Sweep tiling per arithmetic type: faces per block in the second tile
 // direction (x-sweep: pencils along y; y- and z-sweeps: faces along the
@@ -58,6 +61,26 @@ struct SweepCfg {
     static constexpr int MINB = SweepTuning<Real>::MINB;
     using TT = SweepTile<AX, T2>;
     static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+};
+
+// Single-patch sweep in tiles of 32 x T2 faces, FPT per thread (the block
+// is 32 x T2 / FPT threads).
+template <int AX, typename Real, int VAR, int T2, int MINB, int FPT>
+struct SinglePatchSweep {
+    using TT = SweepTile<AX, T2, 32, FPT>;
+    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    static dim3 grid(int nx, int ny, int nz) {
+        if (AX == 0 || AX == 1) return dim3((nx + 31) / 32, (ny + TT::BY - 1) / TT::BY, nz);
+        return dim3((nx + 31) / 32, ny, (nz + TT::BZ - 1) / TT::BZ);
+    }
+    static cudaError_t launch(const SweepArgs<Real> &a, cudaStream_t s) {
+        sweep_kernel<AX, Real, VAR, T2, MINB, FPT><<<grid(a.nx, a.ny, a.nz), dim3(32, TT::ROWS), smem, s>>>(a);
+        return cudaGetLastError();
+    }
 };
 
 // Tile shapes of the batched sweeps (chosen per patch and axis by the
@@ -204,6 +227,10 @@ cudaError_t prepare_sweep_axis() {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<Real, double>::value) {
+        if ((e = SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::prepare()) != cudaSuccess) return e;
+        if ((e = SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::prepare()) != cudaSuccess) return e;
+    }
     if ((e = BatchedSweep<AX, Real, VAR, 0>::prepare()) != cudaSuccess) return e;
     if constexpr (sizeof(Real) == 4) {
         if ((e = BatchedSweep<AX, Real, VAR, 1>::prepare()) != cudaSuccess) return e;
@@ -302,33 +329,54 @@ cudaError_t launch_sweep_batched_impl(int axis, int variant, int tv, const Sweep
     return launch_sweep_batched_axis<2, Real, 1>(tv, a, pgs, tiles, ntiles, s);
 }
 
+// The FP64 sweep keeps one block of 256 threads per SM (its registers), so a
+// small patch fills the GPU only with shorter tiles: 8 high (256 threads, one
+// face each) or 4 high (128 threads, two blocks per SM).  The float sweep
+// always uses its default tile.
+constexpr int kSmallTileHeights[2] = {8, 4};
+
+// blocks of the single-patch sweep along `axis` in tiles t2 high
+inline long long sweep_blocks(int axis, int t2, int nx, int ny, int nz) {
+    const long long bx = (nx + 31) / 32;
+    if (axis == 2) return bx * ny * ((nz + t2 - 1) / t2);
+    return bx * ((ny + t2 - 1) / t2) * nz;     // x- and y-sweeps: t2 pencils or faces along y
+}
+
+// Tile height of the single-patch sweep along `axis`: the default, or for
+// FP64 the tallest of the shorter tiles that gives every SM at least two
+// blocks (the shortest if none does).
+template <typename Real>
+inline int choose_sweep_t2(int axis, int nx, int ny, int nz, int sms) {
+    const int t2d = axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
+    if (!std::is_same<Real, double>::value) return t2d;
+    if (sweep_blocks(axis, t2d, nx, ny, nz) >= 2LL * sms) return t2d;
+    for (int h : kSmallTileHeights)
+        if (sweep_blocks(axis, h, nx, ny, nz) >= 2LL * sms) return h;
+    return kSmallTileHeights[1];
+}
+
 template <int AX, typename Real, int VAR>
-cudaError_t launch_sweep_axis(const SweepArgs<Real> &a, cudaStream_t s) {
+cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) {
     using C = SweepCfg<AX, Real>;
-    constexpr int T2 = C::T2;
-    constexpr int MINB = C::MINB;
-    using TT = typename C::TT;
-    const size_t smem = C::smem;     // allowed by prepare_sweeps() at w5ct_init_grid
-    const dim3 block(32, 8);
-    dim3 grid;
-    if (AX == 0 || AX == 1)
-        grid = dim3((a.nx + 31) / 32, (a.ny + TT::BY - 1) / TT::BY, a.nz);
-    else
-        grid = dim3((a.nx + 31) / 32, a.ny, (a.nz + TT::BZ - 1) / TT::BZ);
-    sweep_kernel<AX, Real, VAR, T2, MINB><<<grid, block, smem, s>>>(a);
-    return cudaGetLastError();
+    if constexpr (std::is_same<Real, double>::value) {
+        if (t2 == 8) return SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::launch(a, s);
+        if (t2 == 4) return SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::launch(a, s);
+    }
+    if (t2 != 0 && t2 != C::T2) return cudaErrorInvalidValue;
+    // the default tile; its shared memory is allowed by prepare_sweeps() at w5ct_init_grid
+    return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::T2 / 8>::launch(a, s);
 }
 
 template <typename Real>
-cudaError_t launch_sweep_impl(int axis, int variant, const SweepArgs<Real> &a, cudaStream_t s) {
+cudaError_t launch_sweep_impl(int axis, int variant, int t2, const SweepArgs<Real> &a, cudaStream_t s) {
     if (variant == 0) {
-        if (axis == 0) return launch_sweep_axis<0, Real, 0>(a, s);
-        if (axis == 1) return launch_sweep_axis<1, Real, 0>(a, s);
-        return launch_sweep_axis<2, Real, 0>(a, s);
+        if (axis == 0) return launch_sweep_axis<0, Real, 0>(t2, a, s);
+        if (axis == 1) return launch_sweep_axis<1, Real, 0>(t2, a, s);
+        return launch_sweep_axis<2, Real, 0>(t2, a, s);
     }
-    if (axis == 0) return launch_sweep_axis<0, Real, 1>(a, s);
-    if (axis == 1) return launch_sweep_axis<1, Real, 1>(a, s);
-    return launch_sweep_axis<2, Real, 1>(a, s);
+    if (axis == 0) return launch_sweep_axis<0, Real, 1>(t2, a, s);
+    if (axis == 1) return launch_sweep_axis<1, Real, 1>(t2, a, s);
+    return launch_sweep_axis<2, Real, 1>(t2, a, s);
 }
 
 }  // namespace w5ct

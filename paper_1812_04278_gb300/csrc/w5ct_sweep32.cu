@@ -5,8 +5,8 @@
 namespace w5ct {
 
 template <>
-cudaError_t launch_sweep<float>(int axis, int variant, const SweepArgs<float> &a, cudaStream_t s) {
-    return launch_sweep_impl<float>(axis, variant, a, s);
+cudaError_t launch_sweep<float>(int axis, int variant, int t2, const SweepArgs<float> &a, cudaStream_t s) {
+    return launch_sweep_impl<float>(axis, variant, t2, a, s);
 }
 
 template <>

@@ -5,8 +5,8 @@
 namespace w5ct {
 
 template <>
-cudaError_t launch_sweep<double>(int axis, int variant, const SweepArgs<double> &a, cudaStream_t s) {
-    return launch_sweep_impl<double>(axis, variant, a, s);
+cudaError_t launch_sweep<double>(int axis, int variant, int t2, const SweepArgs<double> &a, cudaStream_t s) {
+    return launch_sweep_impl<double>(axis, variant, t2, a, s);
 }
 
 template <>
