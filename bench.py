@@ -75,6 +75,8 @@ def parse_args(argv=None):
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sub-records", action="store_true",
+                   help="default workload only: skip the compact batched and adjoint records")
     p.add_argument("--cpu-steps", type=int, default=2, help="oracle steps of the cpu_baseline leg")
     p.add_argument("--workload", default="turb", choices=["turb", "blast", "wave", "batched", "adjoint"],
                    help="turb: 256^3 turbulence, 50 steps (default); blast: 512^3 blast in Mach-5 turbulence, "
@@ -489,6 +491,16 @@ def run_native(args):
         "kernel_src": kernel_source_hash(),
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
+    if not args.no_sub_records and rank == 0 and world == 1:
+        # the other two forms of the path, compact: the 512-patch batch and the
+        # 64^3 adjoint rollout (each also runs alone with --workload)
+        import copy
+        ab = copy.copy(args)
+        ab.n, ab.steps, ab.warmup, ab.err_steps = 256, 5, 3, 3
+        line["batched"] = batched_record(ab, compact=True)
+        aa = copy.copy(args)
+        aa.n, aa.steps = 64, 10
+        line["adjoint"] = adjoint_record(aa, compact=True)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, cons, bface)
     if rank == 0:
@@ -676,6 +688,10 @@ def batch_states(specs, workers):
 
 
 def run_batched(args):
+    print(json.dumps(batched_record(args)))
+
+
+def batched_record(args, compact=False):
     """512 independent periodic patches of uneven sizes (each of nx, ny, nz
     from {16, 24, 32, 48, 64}, seed 1803) with their own turbulent states
     and dts, FP32-bulk, advanced by one context: every step is one replay of
@@ -684,7 +700,8 @@ def run_batched(args):
     FP64 run's per-patch dt sequence, and the patches advanced one context
     per patch (unbatched launches).  Floors rho, P >= 1e-8 are on: the
     supersonic low-beta patches reach P <= 0 within a few steps without them
-    (the oracle's too)."""
+    (the oracle's too).  compact: the record the default benchmark line
+    carries (no model-tile run and no one-context-per-patch run)."""
     from paper_1812_04278_gb300 import inputs
     specs = inputs.patch_batch_spec(npatch=args.patches, seed=1803)
     states = batch_states(specs, min(16, os.cpu_count() or 1))
@@ -722,11 +739,13 @@ def run_batched(args):
     # initial state (the supersonic patches stay physical for about 15 steps
     # from it; the scheme has no protection fluxes)
     b32 = make(w5.W5CT_FP32_BULK)
-    b32.step_graph(args.warmup)
-    torch.cuda.synchronize()
-    ms_model = graph_steps(b32, args.steps)
-    bad_model = b32.status()[1]
     tiles_model = b32.tile_variants().tolist()
+    ms_model, bad_model = float("nan"), 0
+    if not compact:
+        b32.step_graph(args.warmup)
+        torch.cuda.synchronize()
+        ms_model = graph_steps(b32, args.steps)
+        bad_model = b32.status()[1]
     t0 = time.perf_counter()
     b32.autotune(w5.W5CT_TUNE_MEASURE, 3)
     tune_s = time.perf_counter() - t0
@@ -796,6 +815,19 @@ def run_batched(args):
     f32.close()
     del s64
 
+    value = zones * args.steps / (ms32 * 1e-3)
+    sched_values = {SCHEDULES[k]: zones * args.steps / (v * 1e-3) for k, v in ms_sched.items()}
+    if compact:
+        return {"workload": f"{npatch} uneven periodic patches (seed 1803), {zones} zones, FP32-bulk, WENO-Z, "
+                            f"floors on, one CUDA graph replay per step",
+                "value": value, "unit": "zone-updates/s", "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms32 / args.steps, "schedule": SCHEDULES[schedule], "schedule_values": sched_values,
+                "fp64_batched_value": zones * ne / (ms64 * 1e-3),
+                "l1_fp32_vs_fp64": {"mean": float(np.mean(l1s)), "max": float(np.max(l1s)), "steps": ne,
+                                    "fp64_change_mean": float(np.mean(l1c))},
+                "nonphysical": bad + bad_model, "floor_hits": hits, "div_b_linf": divb32,
+                "gpu_launches": launches}
+
     # ---- unbatched: one context per patch, eager steps
     solvers = []
     for p, (c, f) in enumerate(states):
@@ -817,7 +849,6 @@ def run_batched(args):
     for sv in solvers:
         sv.close()
 
-    value = zones * args.steps / (ms32 * 1e-3)
     ach = SWEEP_FLOPS_PER_ZONE[1] * zones / (swms / nsw * 1e-3) / 1e12
     sizes = np.array([np.prod(sh) for sh in shapes])
     line = {
@@ -845,16 +876,20 @@ def run_batched(args):
                   "patches_per_axis_and_variant_model": tiles_model,
                   "model_value": zones * args.steps / (ms_model * 1e-3), "autotune_seconds": tune_s,
                   "schedule": SCHEDULES[schedule],
-                  "schedule_values": {SCHEDULES[k]: zones * args.steps / (v * 1e-3) for k, v in ms_sched.items()}},
+                  "schedule_values": sched_values},
         "unbatched_fp32": {"value": zones * nu / (msu * 1e-3), "ms_per_step": msu / nu, "steps": nu,
                            "contexts": npatch},
         "floor_hits": hits, "nonphysical": bad + bad_model, "div_b_linf": divb32,
         "gpu_launches": launches, "clocks": clocks, "kernel_src": kernel_source_hash(),
     }
-    print(json.dumps(line))
+    return line
 
 
 def run_adjoint(args):
+    print(json.dumps(adjoint_record(args)))
+
+
+def adjoint_record(args, compact=False):
     """Gradient of the L2 misfit after --steps steps (fixed dt = the CFL dt of
     the initial state) with respect to the initial rho, v and edge vector
     potential, on the n^3 oblique circularly polarised Alfven wave (amplitude
@@ -863,7 +898,8 @@ def run_adjoint(args):
     (with per-step checkpoints) and backward times, the adjoint sweep launch
     time, and central-difference checks of a random directional derivative
     (h = 1e-6) on this state and on a textured copy (WENO-Z is not
-    differentiable where a field is exactly uniform)."""
+    differentiable where a field is exactly uniform).  compact: the record
+    the default benchmark line carries (the textured WENO-Z check only)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1812_04278_gb300 import adjoint, build, inputs
@@ -957,7 +993,14 @@ def run_adjoint(args):
                "adjoint_ms_per_step": ms_b / args.steps, "forward_ms_per_step": ms_f / args.steps,
                "one_adjoint_step_ms": ms_adj_step,
                "adjoint_zone_steps_per_s": zones * args.steps / (ms_b * 1e-3)}
-        if name == "fp64":
+        if name == "fp64" and compact:
+            st = solver(prec)
+            _, gt, _, _ = grad(st, pbt, dt)
+            gd, fd, rel = fd_check(st, pbt, dt, gt, 12)
+            rec["fd_check_textured"] = {"g_dot_delta": gd, "central_difference": fd, "rel_err": rel, "h": 1e-6,
+                                        "state": "rho and P textured by 2% smooth modes"}
+            st.close()
+        elif name == "fp64":
             gd, fd, rel = fd_check(s, pb, dt, g, 11)
             rec["fd_check"] = {"g_dot_delta": gd, "central_difference": fd, "rel_err": rel, "h": 1e-6,
                                "state": "the workload's state (uniform rho: WENO-Z weights not differentiable there)"}
@@ -985,6 +1028,16 @@ def run_adjoint(args):
     gd64 = float(sum((g * e).sum() for g, e in zip(grads["fp64"], d)))
     gd32 = float(sum((g * e).sum() for g, e in zip(grads["fp32_bulk"], d)))
     value = out["fp64"]["adjoint_zone_steps_per_s"]
+    if compact:
+        return {"workload": f"{n}^3 circularly polarised Alfven wave + overpressure, gradient of the misfit after "
+                            f"{args.steps} fixed-dt steps in rho, v and the vector potential, WENO-Z, one checkpoint "
+                            f"per step", "value": value, "unit": "adjoint zone-steps/s",
+                "fp64_adjoint_ms_per_step": out["fp64"]["adjoint_ms_per_step"],
+                "fp64_forward_ms_per_step": out["fp64"]["forward_ms_per_step"],
+                "fp32_bulk_value": out["fp32_bulk"]["adjoint_zone_steps_per_s"],
+                "fp32_bulk_adjoint_ms_per_step": out["fp32_bulk"]["adjoint_ms_per_step"],
+                "fd_check_textured_rel_err": out["fp64"]["fd_check_textured"]["rel_err"],
+                "fp32_vs_fp64_grad_max_rel": rel32, "fp32_vs_fp64_directional_rel": abs(gd32 - gd64) / abs(gd64)}
     line = {
         "metric": "adjoint zone-steps/s (gradient of a 10-step rollout misfit, backward pass)", "value": value,
         "unit": "zone-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,

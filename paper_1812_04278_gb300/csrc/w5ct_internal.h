@@ -46,20 +46,24 @@ struct SweepTuning;
 #define W5CT_F64_MINB 1
 #endif
 
+#ifndef W5CT_F32_FPT
+#define W5CT_F32_FPT 2
+#endif
 template <>
 struct SweepTuning<float> {
-    static constexpr int T2X = W5CT_F32_T2X, T2YZ = W5CT_F32_T2YZ, MINB = W5CT_F32_MINB;
+    static constexpr int T2X = W5CT_F32_T2X, T2YZ = W5CT_F32_T2YZ, MINB = W5CT_F32_MINB, FPT = W5CT_F32_FPT;
 };
 template <>
 struct SweepTuning<double> {
-    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = W5CT_F64_MINB;
+    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = W5CT_F64_MINB, FPT = W5CT_F64_T2X / 8;
 };
 
 template <int AX, typename Real>
 struct SweepCfg {
     static constexpr int T2 = AX == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
     static constexpr int MINB = SweepTuning<Real>::MINB;
-    using TT = SweepTile<AX, T2>;
+    static constexpr int FPT = SweepTuning<Real>::FPT;
+    using TT = SweepTile<AX, T2, 32, FPT>;
     static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
 };
 
@@ -224,7 +228,7 @@ struct PersistentLaunch {
 template <int AX, typename Real, int VAR>
 cudaError_t prepare_sweep_axis() {
     using C = SweepCfg<AX, Real>;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB, C::FPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<Real, double>::value) {
@@ -364,7 +368,7 @@ cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) 
     }
     if (t2 != 0 && t2 != C::T2) return cudaErrorInvalidValue;
     // the default tile; its shared memory is allowed by prepare_sweeps() at w5ct_init_grid
-    return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::T2 / 8>::launch(a, s);
+    return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::FPT>::launch(a, s);
 }
 
 template <typename Real>

@@ -136,7 +136,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const Patch
 // One tile per block over a single patch: 32 x T2 / FPT threads (at most
 // 256), FPT faces per thread.
 template <int AX, typename Real, int VAR, int T2, int MINB, int FPT = T2 / 8>
-__global__ void __launch_bounds__(256, MINB) sweep_kernel(SweepArgs<Real> a) {
+__global__ void __launch_bounds__(SweepTile<AX, T2, 32, FPT>::NT, MINB) sweep_kernel(SweepArgs<Real> a) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     PatchGeom pg;
     pg.nx = a.nx;
