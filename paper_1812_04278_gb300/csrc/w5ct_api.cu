@@ -1,5 +1,6 @@
 // w5ct_api.cu -- the C ABI of libw5ct (declared in include/w5ct.h): context,
 // device memory, state transfer, the RK4 + CT step driver, reductions.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -70,6 +71,8 @@ struct w5ct_ctx {
     int *fused_ncb = nullptr, *fused_ntile = nullptr, *fused_done = nullptr, *fused_qa = nullptr;
     int4 *fused_check = nullptr;     // one-item list of w5ct_fused_wait_check
     int fused_blocks = 0;
+    int fused_lag = 0;               // skew of the fused work list in patches (0: phase-major)
+    int fused_group = 16;             // sweep tiles per work item of the fused step
     int pgrid[kMaxTileVariants] = {};   // resident blocks of the persistent sweep per variant
     int *pcounters = nullptr;        // work-queue counters: 4 stages x kMaxTileVariants
     long long sweep_units = 0;       // axis-sweeps covered by the timed event pairs
@@ -383,49 +386,78 @@ int build_fused(w5ct_ctx *c) {
         const PatchGeom &g = c->pg[p];
         ncb[p] = (int)(((long long)g.nx * g.ny * g.nz + kFusedCells - 1) / kFusedCells);
     }
-    // Phase-major within a stage (every patch's cell fields, then CFL blocks
-    // and dts, then sweeps, then updates): an item's dependencies then lie a
-    // whole phase back in the queue and are usually done when it is taken.
+    // The items of each (patch, phase) -- phases 5 s + {0: cell field, 1: CFL
+    // blocks, 2: dt, 3: sweep tiles, 4: update} of stage s -- are ordered by
+    // the key p + lag * phase (ties: the earlier phase first).  With lag >=
+    // npatch this is phase-major (every patch's cell fields, then every
+    // patch's sweeps, then every patch's updates); a smaller lag skews the
+    // list so that the memory-bound updates and cell fields of some patches
+    // run beside the sweeps of others.  Every dependency of an item (the same
+    // patch, an earlier phase) has a smaller key and lies earlier in the
+    // list, so the launch completes whatever the residency.
+    struct Group {
+        long long key;
+        int phase, p;
+        std::vector<int4> items;
+    };
+    std::vector<Group> groups;
+    const long long lag = c->fused_lag > 0 ? c->fused_lag : c->npatch;
+    auto group = [&](int p, int phase) -> std::vector<int4> & {
+        groups.push_back(Group{(long long)p + lag * phase, phase, p, {}});
+        return groups.back().items;
+    };
     for (int st = 0; st < 4; ++st) {
-        for (int p = 0; p < c->npatch; ++p)
-            for (int q = 0; q < ncb[p]; ++q)
-                items.push_back(make_int4(p, fused_tag(FI_CELLB, st, 0, 0), q * kFusedCells, 0));
-        if (st == 0) {
-            for (int p = 0; p < c->npatch; ++p)
-                for (int q = 0; q < ncb[p]; ++q)
-                    items.push_back(make_int4(p, fused_tag(FI_SPEED, 0, 0, 0), q * kFusedCells, 0));
-            for (int p = 0; p < c->npatch; ++p) items.push_back(make_int4(p, fused_tag(FI_DT, 0, 0, 0), 0, 0));
-        }
-        // per patch and axis: the tiles of the patch's tile variant, one per
-        // item; the fused kernel has the two 256-thread variants (0 and 1),
-        // a patch tuned to a narrower one takes the better of the two by
-        // the tile cost model
         for (int p = 0; p < c->npatch; ++p) {
             const PatchGeom &g = c->pg[p];
-            const size_t before = items.size();
+            {
+                std::vector<int4> &it = group(p, 5 * st + 0);
+                for (int q = 0; q < ncb[p]; ++q) it.push_back(make_int4(p, fused_tag(FI_CELLB, st, 0, 0), q * kFusedCells, 0));
+            }
+            if (st == 0) {
+                std::vector<int4> &it = group(p, 1);
+                for (int q = 0; q < ncb[p]; ++q) it.push_back(make_int4(p, fused_tag(FI_SPEED, 0, 0, 0), q * kFusedCells, 0));
+                group(p, 2).push_back(make_int4(p, fused_tag(FI_DT, 0, 0, 0), 0, 0));
+            }
+            // per axis: the tiles of one of the fused kernel's tile variants
+            // (one tile per block; float: 32 x 8, 16 x 16, 8 x 16), the one
+            // with the least padded lanes and rows and halo share by the
+            // tile cost model, one tile per item
+            std::vector<int4> &sw = group(p, 5 * st + 3);
             for (int a = 0; a < 3; ++a) {
-                int v = c->pvar[a][p];
-                if (v > 1) {
-                    int b0, h0, b1, h1;
-                    variant_shape(c, a, 0, b0, h0);
-                    variant_shape(c, a, 1, b1, h1);
-                    v = tile_model_cost(g, a, b1, h1) < tile_model_cost(g, a, b0, h0) ? 1 : 0;
+                const int nfv = fp64 ? fused_variants<double>() : fused_variants<float>();
+                int v = 0, bx = 0, t2 = 0;
+                double best = 0;
+                for (int w = 0; w < nfv; ++w) {
+                    int bw, hw;
+                    if (fp64)
+                        fused_tile_shape<double>(w, bw, hw);
+                    else
+                        fused_tile_shape<float>(w, bw, hw);
+                    const double cost = tile_model_cost(g, a, bw, hw);
+                    if (w == 0 || cost < best * (1.0 - 1e-9)) {
+                        best = cost;
+                        v = w;
+                        bx = bw;
+                        t2 = hw;
+                    }
                 }
-                int bx, t2;
-                variant_shape(c, a, v, bx, t2);
                 const long long nbx = (g.nx + bx - 1) / bx;
                 const long long nb1 = a == 2 ? g.ny : (g.ny + t2 - 1) / t2;
                 const long long nb2 = a == 2 ? (g.nz + t2 - 1) / t2 : g.nz;
                 const long long ntiles = nbx * nb1 * nb2;
-                for (long long L = 0; L < ntiles; ++L)
-                    items.push_back(make_int4(p, fused_tag(FI_SWEEP, st, a, v), (int)L, 0));
+                const long long grp = c->fused_group > 0 ? c->fused_group : 1;
+                for (long long L = 0; L < ntiles; L += grp)
+                    sw.push_back(make_int4(p, fused_tag(FI_SWEEP, st, a, v), (int)L, (int)std::min(grp, ntiles - L)));
             }
-            if (st == 0) ntile[p] = (int)(items.size() - before);
+            if (st == 0) ntile[p] = (int)sw.size();
+            std::vector<int4> &up = group(p, 5 * st + 4);
+            for (int q = 0; q < ncb[p]; ++q) up.push_back(make_int4(p, fused_tag(FI_UPDATE, st, 0, 0), q * kFusedCells, 0));
         }
-        for (int p = 0; p < c->npatch; ++p)
-            for (int q = 0; q < ncb[p]; ++q)
-                items.push_back(make_int4(p, fused_tag(FI_UPDATE, st, 0, 0), q * kFusedCells, 0));
     }
+    std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) {
+        return x.key != y.key ? x.key < y.key : x.phase < y.phase;
+    });
+    for (const Group &gr : groups) items.insert(items.end(), gr.items.begin(), gr.items.end());
     if (items.size() > (size_t)0x7fffffff) return fail(c, W5CT_ERR_ARG, "too many work items for the fused step");
     const size_t P = (size_t)c->npatch;
     size_t bytes = 0;

@@ -43,26 +43,89 @@ namespace w5ct {
 
 enum FusedItem { FI_CELLB = 0, FI_SPEED = 1, FI_DT = 2, FI_SWEEP = 3, FI_UPDATE = 4 };
 
-// cells of one cell-wise item (four per thread of a 256-thread block): the
-// per-item bookkeeping (queue, dependency check, fence, counter) is then
-// shared by 1024 cells
+// cells of one cell-wise item (eight per thread of a float block, four of a
+// double block): the per-item bookkeeping (queue, dependency check, fence,
+// counter) is then shared by 1024 cells
 constexpr int kFusedCells = 1024;
 
 // item: x = patch, y = type | stage << 3 | axis << 5 | v << 8; for a sweep
-// item z = tile index i + nbx (j + nb1 k) among the patch's tiles of variant
-// v along the axis (the order of the tile tables), for a cell-wise item z =
-// its first cell; w = 0
+// item z = the first of its w tiles, tile index i + nbx (j + nb1 k) among the
+// patch's tiles of variant v along the axis; for a cell-wise item z = its
+// first cell and w = 0
 __host__ __device__ inline int fused_tag(int type, int stage, int axis, int v) {
     return type | (stage << 3) | (axis << 5) | (v << 8);
 }
 
-// Tile variant V (0 or 1: 256 threads, the fused kernel's block) of the
-// sweep along AX and its shared memory.
+// Block of the fused kernel: in float 128 threads, four blocks per SM (the
+// register budget of the float sweep, 128 per thread), so that the 8-lane
+// tiles that suit patches 16, 24 or 48 cells wide need no sub-tiles; in
+// double 256 threads, one block per SM (255 registers).
+template <typename Real>
+struct FusedBlock {
+    static constexpr int NT = sizeof(Real) == 4 ? 128 : 256;
+    static constexpr int MINB = sizeof(Real) == 4 ? 4 : 1;
+};
+
+// Sweep tiles of the fused kernel (lanes along x BX, faces or pencils T2 in
+// the second direction, FPT per thread; BX x T2 / FPT = the block):
+//   float   0: 32 x 8 (2 per thread)   1: 16 x 16 (2)   2: 8 x 16 (1)
+//   double  0: 32 x 16 (2)
+template <typename Real, int V>
+struct FusedShape;
+template <>
+struct FusedShape<float, 0> {
+    static constexpr int BX = 32, T2 = 8, FPT = 2;
+};
+template <>
+struct FusedShape<float, 1> {
+    static constexpr int BX = 16, T2 = 16, FPT = 2;
+};
+template <>
+struct FusedShape<float, 2> {
+    static constexpr int BX = 8, T2 = 16, FPT = 1;
+};
+template <>
+struct FusedShape<double, 0> {
+    static constexpr int BX = 32, T2 = 16, FPT = 2;
+};
+
+template <typename Real>
+constexpr int fused_variants() {
+    return sizeof(Real) == 4 ? 3 : 1;
+}
+
+// (BX, T2) of fused tile variant v (host side, for the work list)
+template <typename Real>
+inline void fused_tile_shape(int v, int &bx, int &t2) {
+    if (sizeof(Real) == 8 || v == 0) {
+        bx = 32;
+        t2 = sizeof(Real) == 8 ? 16 : 8;
+    } else {
+        bx = v == 1 ? 16 : 8;
+        t2 = 16;
+    }
+}
+
+// (BX, T2, FPT) of fused tile variant v (device side)
+template <typename Real>
+__device__ __forceinline__ void fused_shape_rt(int v, int &bx, int &t2, int &fpt) {
+    if constexpr (sizeof(Real) == 4) {
+        bx = v == 0 ? FusedShape<float, 0>::BX : v == 1 ? FusedShape<float, 1>::BX : FusedShape<float, 2>::BX;
+        t2 = v == 0 ? FusedShape<float, 0>::T2 : v == 1 ? FusedShape<float, 1>::T2 : FusedShape<float, 2>::T2;
+        fpt = v == 0 ? FusedShape<float, 0>::FPT : v == 1 ? FusedShape<float, 1>::FPT : FusedShape<float, 2>::FPT;
+    } else {
+        bx = FusedShape<double, 0>::BX;
+        t2 = FusedShape<double, 0>::T2;
+        fpt = FusedShape<double, 0>::FPT;
+    }
+}
+
+// Tile variant V of the sweep along AX and its shared memory.
 template <typename Real, int AX, int V>
 struct FusedTile {
-    using C = TileV<AX, Real, V>;
-    using TT = SweepTile<AX, C::T2, C::BX, C::FPT>;
-    static_assert(TT::NT == 256, "one tile per 256-thread block");
+    using S = FusedShape<Real, V>;
+    using TT = SweepTile<AX, S::T2, S::BX, S::FPT>;
+    static_assert(TT::NT == FusedBlock<Real>::NT, "one tile per block");
     static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
 };
 
@@ -141,23 +204,9 @@ __device__ __forceinline__ void fused_cellb(const PatchGeom &g, int i, int j, in
     Bz[p] = (Real(9) * (bz[p + zm1] + bz[p]) - (bz[p + zm2] + bz[p + zp1])) * s;
 }
 
-// Tile L of variant V (0 or 1: one tile of 256 threads per block) of a
-// patch along AX.
-template <int AX, typename Real, int VAR, int V>
-__device__ __forceinline__ void fused_sweep(const SweepArgs<Real> &a, const PatchGeom &pg, int L, int tid, Real *sm) {
-    using Cv = typename FusedTile<Real, AX, V>::C;
-    const int nbx = (pg.nx + Cv::BX - 1) / Cv::BX;
-    const int nb1 = AX == 2 ? pg.ny : (pg.ny + Cv::T2 - 1) / Cv::T2;
-    const int r = L / nbx;
-    const int i = L - r * nbx, k = r / nb1, j = r - k * nb1;
-    // blockDim = (32, 8): variant 0 uses the block's own thread indices
-    const int tx = Cv::BX == 32 ? (int)threadIdx.x : tid % Cv::BX;
-    const int ty = Cv::BX == 32 ? (int)threadIdx.y : tid / Cv::BX;
-    sweep_tile_at<AX, Real, VAR, Cv::T2, Cv::BX, Cv::FPT>(a, pg, i, j, k, sm, tx, ty);
-}
-
 template <typename Real, int VAR>
-__global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kernel(FusedArgs<Real> A) {
+__global__ void __launch_bounds__(FusedBlock<Real>::NT, FusedBlock<Real>::MINB) fused_step_kernel(FusedArgs<Real> A) {
+    constexpr int NT = FusedBlock<Real>::NT;
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     __shared__ int s_item, s_ok;
     __shared__ double s_red[3 * 32];
@@ -202,23 +251,20 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
         // ---- the item's work
         int *done = nullptr;
         if (type == FI_SWEEP) {
-            if constexpr (sizeof(Real) == 4) {
-                switch (axis * 2 + v) {
-                    case 0: fused_sweep<0, Real, VAR, 0>(A.a[0], pg, t.z, tid, sm); break;
-                    case 1: fused_sweep<0, Real, VAR, 1>(A.a[0], pg, t.z, tid, sm); break;
-                    case 2: fused_sweep<1, Real, VAR, 0>(A.a[1], pg, t.z, tid, sm); break;
-                    case 3: fused_sweep<1, Real, VAR, 1>(A.a[1], pg, t.z, tid, sm); break;
-                    case 4: fused_sweep<2, Real, VAR, 0>(A.a[2], pg, t.z, tid, sm); break;
-                    default: fused_sweep<2, Real, VAR, 1>(A.a[2], pg, t.z, tid, sm); break;
-                }
-            } else {
-                // the FP64 sweeps have one tile shape
-                if (axis == 0)
-                    fused_sweep<0, Real, VAR, 0>(A.a[0], pg, t.z, tid, sm);
-                else if (axis == 1)
-                    fused_sweep<1, Real, VAR, 0>(A.a[1], pg, t.z, tid, sm);
-                else
-                    fused_sweep<2, Real, VAR, 0>(A.a[2], pg, t.z, tid, sm);
+            // t.w consecutive tiles from t.z (one item's bookkeeping for all);
+            // one copy of the sweep code for every axis and tile shape
+            int bx, t2, fpt;
+            fused_shape_rt<Real>(v, bx, t2, fpt);
+            const SweepArgs<Real> &a = A.a[axis];
+            const int nbx = (pg.nx + bx - 1) / bx;
+            const int nb1 = axis == 2 ? pg.ny : (pg.ny + t2 - 1) / t2;
+#pragma unroll 1
+            for (int q = 0; q < t.w; ++q) {
+                if (q > 0) __syncthreads();          // the tile box in shared memory is reused
+                const int L = t.z + q;
+                const int r = L / nbx;
+                const int i = L - r * nbx, k = r / nb1, j = r - k * nb1;
+                sweep_tile_rt<Real, VAR>(a, pg, axis, bx, t2, fpt, i, j, k, sm, tid % bx, tid / bx);
             }
             done = C.sweep(stage, p);
         } else if (type == FI_DT) {
@@ -234,12 +280,12 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
             done = C.dtc(p);
         } else {
             // kFusedCells consecutive cells of the patch (storage order),
-            // cells t.z + tid + 256 r
+            // cells t.z + tid + NT r
             const int ncell = pg.nx * pg.ny * pg.nz;
             if (type == FI_CELLB) {
 #pragma unroll 1
-                for (int r = 0; r < kFusedCells / 256; ++r) {
-                    const int idx = t.z + tid + 256 * r;
+                for (int r = 0; r < kFusedCells / NT; ++r) {
+                    const int idx = t.z + tid + NT * r;
                     if (idx < ncell) {
                         const int row = idx / pg.nx;
                         const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
@@ -252,8 +298,8 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
                     double v[3] = {0.0, 0.0, 0.0};
                     bool bad = false;
 #pragma unroll 1
-                    for (int r = 0; r < kFusedCells / 256; ++r) {
-                        const int idx = t.z + tid + 256 * r;
+                    for (int r = 0; r < kFusedCells / NT; ++r) {
+                        const int idx = t.z + tid + NT * r;
                         if (idx < ncell) {
                             const size_t q = (size_t)pg.off + (size_t)idx;
                             const SweepArgs<Real> &a = A.a[0];
@@ -262,7 +308,7 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
                         }
                     }
                     if (bad) atomicOr(A.a[0].flag, 1);
-                    // maxima over the block's eight warps
+                    // maxima over the block's NT / 32 warps
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -272,7 +318,7 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
                     __syncthreads();
                     if (tid < 32) {
                         for (int d = 0; d < 3; ++d) {
-                            double x = tid < 8 ? s_red[d * 32 + tid] : 0.0;
+                            double x = tid < NT / 32 ? s_red[d * 32 + tid] : 0.0;
 #pragma unroll
                             for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
                             if (tid == 0) atomicMax(&A.smax[3 * p + d], (unsigned long long)__double_as_longlong(x));
@@ -285,17 +331,12 @@ __global__ void __launch_bounds__(256, SweepTuning<Real>::MINB) fused_step_kerne
                                           (Real)pg.rdz, pg.rdx, pg.rdy, pg.rdz};
                 const double dt = A.dts[p];
 #pragma unroll 1
-                for (int r = 0; r < kFusedCells / 256; ++r) {
-                    const int idx = t.z + tid + 256 * r;
+                for (int r = 0; r < kFusedCells / NT; ++r) {
+                    const int idx = t.z + tid + NT * r;
                     if (idx >= ncell) break;
                     const int row = idx / pg.nx;
                     const int i = idx - row * pg.nx, k = row / pg.ny, j = row - k * pg.ny;
-                    switch (stage) {
-                        case 0: update_cell<Real, 0>(A.u, ug, i, j, k, dt); break;
-                        case 1: update_cell<Real, 1>(A.u, ug, i, j, k, dt); break;
-                        case 2: update_cell<Real, 2>(A.u, ug, i, j, k, dt); break;
-                        default: update_cell<Real, 3>(A.u, ug, i, j, k, dt); break;
-                    }
+                    update_cell_rt<Real>(A.u, ug, i, j, k, dt, stage);
                 }
                 done = C.update(stage, p);
             }
@@ -321,12 +362,15 @@ constexpr size_t fused_smem_v() {
     return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
-// shared memory of the fused kernel: the largest item (variants 0..3 in
+// shared memory of the fused kernel: the largest item (variants 0..2 in
 // float, 0 in double)
 template <typename Real, int VAR>
 size_t fused_smem() {
     size_t m = fused_smem_v<Real, 0>();
-    if (sizeof(Real) == 4 && fused_smem_v<Real, 1>() > m) m = fused_smem_v<Real, 1>();
+    if constexpr (sizeof(Real) == 4) {
+        if (fused_smem_v<Real, 1>() > m) m = fused_smem_v<Real, 1>();
+        if (fused_smem_v<Real, 2>() > m) m = fused_smem_v<Real, 2>();
+    }
     return m;
 }
 
@@ -338,14 +382,15 @@ cudaError_t fused_grid_impl(int &blocks, size_t &smem) {
     int dev = 0, sms = 0, per = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fused_step_kernel<Real, VAR>, 256, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fused_step_kernel<Real, VAR>, FusedBlock<Real>::NT, smem);
     blocks = sms * (per > 0 ? per : 1);
     return e;
 }
 
 template <typename Real, int VAR>
 cudaError_t launch_fused_impl(const FusedArgs<Real> &A, int blocks, cudaStream_t s) {
-    fused_step_kernel<Real, VAR><<<blocks, dim3(32, 8), fused_smem<Real, VAR>(), s>>>(A);
+    fused_step_kernel<Real, VAR><<<blocks, dim3(32, FusedBlock<Real>::NT / 32), fused_smem<Real, VAR>(), s>>>(A);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,84 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
     }
 }
 
+// sweep_tile_at with the axis and the tile shape (BX lanes, T2 faces or
+// pencils, FPT faces per thread) known only at run time: one copy of the
+// face arithmetic serves every shape, for a kernel that runs all of them
+// (the fused step, whose instruction cache would not hold nine inlined
+// copies).  Outputs go to the flux planes of `a` (the sweep's arguments for
+// axis ax).  Same arithmetic per face as sweep_tile_at.
+template <typename Real, int VAR>
+__device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const PatchGeom &pg, int ax, int BX, int T2,
+                                              int FPT, int tbx, int tby, int tbz, Real *sm, int tx, int ty) {
+    const int nx = pg.nx, ny = pg.ny, nz = pg.nz;
+    const size_t off = (size_t)pg.off;
+    const int ROWS = T2 / FPT, NT = BX * ROWS;
+    const int BY = ax == 2 ? 1 : T2, BZ = ax == 2 ? T2 : 1;
+    const int CX = BX + (ax == 0 ? 5 : 0), CY = BY + (ax == 1 ? 5 : 0), CZ = BZ + (ax == 2 ? 5 : 0);
+    const int NC = CX * CY * CZ;
+    const int ST = ax == 0 ? 1 : (ax == 1 ? CX : CX * CY);
+    const int x0 = tbx * BX, y0 = tby * BY, z0 = tbz * BZ;
+    const int ox = x0 - (ax == 0 ? 2 : 0), oy = y0 - (ax == 1 ? 2 : 0), oz = z0 - (ax == 2 ? 2 : 0);
+    const int tid = tx + BX * ty;
+
+    // phase 1: per-cell quantities of the cell box; the box coordinates of
+    // cell c = tid + r NT are stepped by NT with carries (no division per cell)
+    bool bad = false, hit = false;
+    {
+        const int cxy = CX * CY;
+        int cz = tid / cxy, rem = tid - cz * cxy;
+        int cy = rem / CX, cx = rem - cy * CX;
+        const int sz = NT / cxy, srem = NT - sz * cxy;
+        const int sy = srem / CX, sx = srem - sy * CX;
+        for (int c = tid; c < NC; c += NT) {
+            const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
+            const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+            cell_fill_axis<Real>(sm + c, NC, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g], a.bc[0][g],
+                                 a.bc[1][g], a.bc[2][g], ax, a.K, bad, hit);
+            cx += sx;
+            int carry = cx >= CX;
+            cx -= carry ? CX : 0;
+            cy += sy + carry;
+            carry = cy >= CY;
+            cy -= carry ? CY : 0;
+            cz += sz + carry;
+        }
+    }
+    if (bad) atomicOr(a.flag, 1);
+    if (a.K.floors) {
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if ((tid & 31) == 0 && m) atomicAdd(a.hits, (unsigned long long)__popc(m));
+    }
+    __syncthreads();
+
+    // phase 2: FPT interfaces per thread
+#pragma unroll 1
+    for (int r = 0; r < FPT; ++r) {
+        const int t2 = ty + ROWS * r;
+        const int bx = tx;
+        const int by = ax == 2 ? 0 : t2;
+        const int bz = ax == 2 ? t2 : 0;
+        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+        if (gx < nx && gy < ny && gz < nz) {
+            const int c0 = bx + CX * (by + CY * bz);   // stencil cell i-2
+            Real Ff[7], s1, s2;
+            face_flux<Real, VAR>(sm + c0, NC, ST, a.K, Ff, s1, s2);
+            const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+            // lab components of the frame momentum flux (n, t1, t2)
+            Real *const fn = ax == 0 ? a.F[1] : (ax == 1 ? a.F[2] : a.F[3]);
+            Real *const f1 = ax == 0 ? a.F[2] : (ax == 1 ? a.F[3] : a.F[1]);
+            Real *const f2 = ax == 0 ? a.F[3] : (ax == 1 ? a.F[1] : a.F[2]);
+            a.F[0][g] = Ff[0];
+            fn[g] = Ff[1];
+            f1[g] = Ff[2];
+            f2[g] = Ff[3];
+            a.F[4][g] = Ff[6];
+            a.S[0][g] = s1;
+            a.S[1][g] = s2;
+        }
+    }
+}
+
 // One tile computed by the whole block, blockDim = (BX, ROWS).
 template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8>
 __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
@@ -332,9 +410,12 @@ __device__ __forceinline__ Real from_double(double x) {
         return (Real)x;
 }
 
-template <typename Real, int STAGE>
-__device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const UpdGeom<Real> &ug, int i, int j, int k,
-                                            double dt) {
+// One cell's update at RK stage STAGE (0..3, a run-time value here);
+// update_cell<Real, STAGE> below is the same with the stage fixed at compile
+// time.
+template <typename Real>
+__device__ __forceinline__ void update_cell_rt(const UpdateArgs<Real> &a, const UpdGeom<Real> &ug, int i, int j, int k,
+                                               double dt, int STAGE) {
     const int nx = ug.nx, ny = ug.ny, nz = ug.nz;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i + 1 < nx ? i + 1 : 0;
     const int jm = j > 0 ? j - 1 : ny - 1, jp = j + 1 < ny ? j + 1 : 0;
@@ -345,7 +426,9 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
     const long long p = (long long)ug.off + i + sy * j + sz * k;
     const long long xm = im - i, xp = ip - i, ym = (jm - j) * sy, yp = (jp - j) * sy, zm = (km - k) * sz,
                     zp = (kp - k) * sz;
-    constexpr double c = StageW<STAGE>::c, wc = StageW<STAGE>::wc;
+    const double c = STAGE == 0 ? StageW<0>::c : STAGE == 1 ? StageW<1>::c : STAGE == 2 ? StageW<2>::c : StageW<3>::c;
+    const double wc = STAGE == 0 ? StageW<0>::wc : STAGE == 1 ? StageW<1>::wc : STAGE == 2 ? StageW<2>::wc
+                                                                                          : StageW<3>::wc;
 
     // Every load of this thread is issued before its first store, so that
     // they can all be in flight together (the compiler cannot move a load
@@ -460,6 +543,12 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const Upd
             if (kCopy) a.b0r[f][p] = br;
         }
     }
+}
+
+template <typename Real, int STAGE>
+__device__ __forceinline__ void update_cell(const UpdateArgs<Real> &a, const UpdGeom<Real> &ug, int i, int j, int k,
+                                            double dt) {
+    update_cell_rt<Real>(a, ug, i, j, k, dt, STAGE);
 }
 
 template <typename Real, int STAGE>

@@ -111,21 +111,18 @@ __device__ __forceinline__ void speeds(Real cs2, Real ca2, Real bt2, Real &fmc, 
 }
 
 // ---------------------------------------------------------------- one cell
-// Fills the NCQ per-cell quantities of a cell for a sweep along axis AX
-// (frame (n, t1, t2) = (AX, AX+1, AX+2) mod 3).  sm points at the cell's
-// slot of quantity 0; quantities are `stride` elements apart.
-template <typename Real, int AX>
-__device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real mx, Real my, Real mz, Real E,
-                                          Real Bx, Real By, Real Bz, const Phys<Real> &K, bool &bad, bool &hit) {
+// Fills the NCQ per-cell quantities of a cell from its state in the sweep
+// frame (n, t1, t2): momentum (mn, m1, m2), cell field (Bn, B1, B2).  sm
+// points at the cell's slot of quantity 0; quantities are `stride` elements
+// apart.
+template <typename Real>
+__device__ __forceinline__ void cell_fill_frame(Real *sm, int stride, Real rho, Real mn, Real m1, Real m2, Real E,
+                                                Real Bn, Real B1, Real B2, const Phys<Real> &K, bool &bad, bool &hit) {
     using m = M<Real>;
-    constexpr int n = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
-    const Real mm[3] = {mx, my, mz};
-    const Real BB3[3] = {Bx, By, Bz};
     Real r = rho;
     if (K.floors && r < K.rho_min) { r = K.rho_min; hit = true; }
     const Real ir = m::rcp_(r);
-    const Real vn = mm[n] * ir, v1 = mm[t1] * ir, v2 = mm[t2] * ir;
-    const Real Bn = BB3[n], B1 = BB3[t1], B2 = BB3[t2];
+    const Real vn = mn * ir, v1 = m1 * ir, v2 = m2 * ir;
     const Real vv = vn * vn + v1 * v1 + v2 * v2;
     const Real BB = Bn * Bn + B1 * B1 + B2 * B2;
     Real P = K.gm1 * (E - Real(0.5) * r * vv - Real(0.5) * BB);
@@ -142,9 +139,9 @@ __device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real m
     sm[C_BT2 * stride] = B2;
     sm[C_P * stride] = P;
     sm[C_RHOQ * stride] = rho;
-    sm[C_MN * stride] = mm[n];
-    sm[C_MT1 * stride] = mm[t1];
-    sm[C_MT2 * stride] = mm[t2];
+    sm[C_MN * stride] = mn;
+    sm[C_MT1 * stride] = m1;
+    sm[C_MT2 * stride] = m2;
     sm[C_E * stride] = E;
     sm[C_F0 * stride] = r * vn;
     sm[C_F1 * stride] = r * vn * vn + Pt - Bn * Bn;
@@ -161,6 +158,31 @@ __device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real m
     sm[C_CF * stride] = m::sqrt_(cf2);
     sm[C_CA * stride] = m::abs_(Bn) * (m::sqrt_(r) * ir);     // |B_n| / sqrt(rho)
     sm[C_CSL * stride] = m::sqrt_(csl2);
+}
+
+// cell_fill_frame for a sweep along axis AX (frame (n, t1, t2) = (AX, AX+1,
+// AX+2) mod 3) from the lab components
+template <typename Real, int AX>
+__device__ __forceinline__ void cell_fill(Real *sm, int stride, Real rho, Real mx, Real my, Real mz, Real E,
+                                          Real Bx, Real By, Real Bz, const Phys<Real> &K, bool &bad, bool &hit) {
+    constexpr int n = AX, t1 = (AX + 1) % 3, t2 = (AX + 2) % 3;
+    const Real mm[3] = {mx, my, mz};
+    const Real BB3[3] = {Bx, By, Bz};
+    cell_fill_frame<Real>(sm, stride, rho, mm[n], mm[t1], mm[t2], E, BB3[n], BB3[t1], BB3[t2], K, bad, hit);
+}
+
+// the same with the axis known only at run time (selects, no indexed arrays)
+template <typename Real>
+__device__ __forceinline__ void cell_fill_axis(Real *sm, int stride, Real rho, Real mx, Real my, Real mz, Real E,
+                                               Real Bx, Real By, Real Bz, int ax, const Phys<Real> &K, bool &bad,
+                                               bool &hit) {
+    const Real mn = ax == 0 ? mx : (ax == 1 ? my : mz);
+    const Real m1 = ax == 0 ? my : (ax == 1 ? mz : mx);
+    const Real m2 = ax == 0 ? mz : (ax == 1 ? mx : my);
+    const Real Bn = ax == 0 ? Bx : (ax == 1 ? By : Bz);
+    const Real B1 = ax == 0 ? By : (ax == 1 ? Bz : Bx);
+    const Real B2 = ax == 0 ? Bz : (ax == 1 ? Bx : By);
+    cell_fill_frame<Real>(sm, stride, rho, mn, m1, m2, E, Bn, B1, B2, K, bad, hit);
 }
 
 // fast signal speed |v_d| + c_f^d of a cell along axis d (Eq. cfl)
