@@ -120,14 +120,32 @@ __device__ __forceinline__ void fused_shape_rt(int v, int &bx, int &t2, int &fpt
     }
 }
 
-// Tile variant V of the sweep along AX and its shared memory.
+// Tile variant V of the sweep along AX: its cell box (cells along the axis x
+// pencils, sweep_tile_rt's layout)
 template <typename Real, int AX, int V>
 struct FusedTile {
     using S = FusedShape<Real, V>;
-    using TT = SweepTile<AX, S::T2, S::BX, S::FPT>;
-    static_assert(TT::NT == FusedBlock<Real>::NT, "one tile per block");
-    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static_assert(S::BX * (S::T2 / S::FPT) == FusedBlock<Real>::NT, "one tile per block");
+    static constexpr int cells = ((AX == 0 ? S::BX : S::T2) + 5) * (AX == 0 ? S::T2 : S::BX);
 };
+
+template <typename Real, int V>
+__host__ __device__ constexpr int fused_cells_v() {
+    constexpr int a = FusedTile<Real, 0, V>::cells, b = FusedTile<Real, 1, V>::cells, c = FusedTile<Real, 2, V>::cells;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+// the quantity stride of the fused kernel's cell box: the largest box of its
+// tile variants (float 416 cells, double 672)
+template <typename Real>
+__host__ __device__ constexpr int fused_nqs() {
+    if constexpr (sizeof(Real) == 4) {
+        constexpr int a = fused_cells_v<float, 0>(), b = fused_cells_v<float, 1>(), c = fused_cells_v<float, 2>();
+        return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    } else {
+        return fused_cells_v<double, 0>();
+    }
+}
 
 // Per-patch completion counters, zeroed at the start of every step:
 // cellb[s][p], sweep[s][p], update[s][p], speed[p], dt[p].
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(FusedBlock<Real>::NT, FusedBlock<Real>::MINB) 
                 const int L = t.z + q;
                 const int r = L / nbx;
                 const int i = L - r * nbx, k = r / nb1, j = r - k * nb1;
-                sweep_tile_rt<Real, VAR>(a, pg, axis, bx, t2, fpt, i, j, k, sm, tid % bx, tid / bx);
+                sweep_tile_rt<Real, VAR, fused_nqs<Real>()>(a, pg, axis, bx, t2, fpt, i, j, k, sm, tid % bx, tid / bx);
             }
             done = C.sweep(stage, p);
         } else if (type == FI_DT) {
@@ -356,22 +374,10 @@ cudaError_t launch_fused_step(int variant, const FusedArgs<Real> &A, int blocks,
 template <typename Real>
 cudaError_t fused_grid(int variant, int &blocks, size_t &smem);
 
-template <typename Real, int V>
-constexpr size_t fused_smem_v() {
-    constexpr size_t a = FusedTile<Real, 0, V>::smem, b = FusedTile<Real, 1, V>::smem, c = FusedTile<Real, 2, V>::smem;
-    return a > b ? (a > c ? a : c) : (b > c ? b : c);
-}
-
-// shared memory of the fused kernel: the largest item (variants 0..2 in
-// float, 0 in double)
+// shared memory of the fused kernel: the cell box of its largest sweep tile
 template <typename Real, int VAR>
 size_t fused_smem() {
-    size_t m = fused_smem_v<Real, 0>();
-    if constexpr (sizeof(Real) == 4) {
-        if (fused_smem_v<Real, 1>() > m) m = fused_smem_v<Real, 1>();
-        if (fused_smem_v<Real, 2>() > m) m = fused_smem_v<Real, 2>();
-    }
-    return m;
+    return (size_t)fused_nqs<Real>() * NCQ * sizeof(Real);
 }
 
 template <typename Real, int VAR>

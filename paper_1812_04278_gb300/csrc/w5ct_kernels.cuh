@@ -130,43 +130,47 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
 // pencils, FPT faces per thread) known only at run time: one copy of the
 // face arithmetic serves every shape, for a kernel that runs all of them
 // (the fused step, whose instruction cache would not hold nine inlined
-// copies).  Outputs go to the flux planes of `a` (the sweep's arguments for
-// axis ax).  Same arithmetic per face as sweep_tile_at.
-template <typename Real, int VAR>
+// copies).  The cell box is stored sweep-axis-major -- cell (s, p) at
+// s + CS p, s along the sweep axis (CS = faces along the axis + 5), p the
+// pencil -- and quantity q of a cell NQS elements after quantity q - 1: the
+// stencil stride is 1 and the quantity stride the compile-time NQS (at
+// least the largest box, CS x pencils), so the face arithmetic's shared
+// loads take constant offsets whatever the shape.  Outputs go to the flux
+// planes of `a` (the sweep's arguments for axis ax).  Same arithmetic per
+// face as sweep_tile_at.
+template <typename Real, int VAR, int NQS>
 __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const PatchGeom &pg, int ax, int BX, int T2,
                                               int FPT, int tbx, int tby, int tbz, Real *sm, int tx, int ty) {
     const int nx = pg.nx, ny = pg.ny, nz = pg.nz;
     const size_t off = (size_t)pg.off;
     const int ROWS = T2 / FPT, NT = BX * ROWS;
     const int BY = ax == 2 ? 1 : T2, BZ = ax == 2 ? T2 : 1;
-    const int CX = BX + (ax == 0 ? 5 : 0), CY = BY + (ax == 1 ? 5 : 0), CZ = BZ + (ax == 2 ? 5 : 0);
-    const int NC = CX * CY * CZ;
-    const int ST = ax == 0 ? 1 : (ax == 1 ? CX : CX * CY);
     const int x0 = tbx * BX, y0 = tby * BY, z0 = tbz * BZ;
-    const int ox = x0 - (ax == 0 ? 2 : 0), oy = y0 - (ax == 1 ? 2 : 0), oz = z0 - (ax == 2 ? 2 : 0);
+    const int CS = (ax == 0 ? BX : T2) + 5;          // cells along the sweep axis
+    const int NPC = ax == 0 ? T2 : BX;              // pencils
+    const int NCELL = CS * NPC;
     const int tid = tx + BX * ty;
 
-    // phase 1: per-cell quantities of the cell box; the box coordinates of
-    // cell c = tid + r NT are stepped by NT with carries (no division per cell)
+    // phase 1: per-cell quantities of the cell box, traversed x fastest
+    // (coalesced loads): the x-sweep's fastest box index is s, the y- and
+    // z-sweeps' is p; stepped by NT with a carry (no division per cell)
     bool bad = false, hit = false;
     {
-        const int cxy = CX * CY;
-        int cz = tid / cxy, rem = tid - cz * cxy;
-        int cy = rem / CX, cx = rem - cy * CX;
-        const int sz = NT / cxy, srem = NT - sz * cxy;
-        const int sy = srem / CX, sx = srem - sy * CX;
-        for (int c = tid; c < NC; c += NT) {
-            const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
+        const int F = ax == 0 ? CS : NPC;
+        int fi = tid % F, si = tid / F;
+        const int df = NT % F, ds = NT / F;
+        for (int c = tid; c < NCELL; c += NT) {
+            const int sa = ax == 0 ? fi : si, p = ax == 0 ? si : fi;
+            const int gx = wrapi(ax == 0 ? x0 - 2 + sa : x0 + p, nx);
+            const int gy = wrapi(ax == 1 ? y0 - 2 + sa : (ax == 0 ? y0 + p : y0), ny);
+            const int gz = wrapi(ax == 2 ? z0 - 2 + sa : z0, nz);
             const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
-            cell_fill_axis<Real>(sm + c, NC, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g], a.bc[0][g],
-                                 a.bc[1][g], a.bc[2][g], ax, a.K, bad, hit);
-            cx += sx;
-            int carry = cx >= CX;
-            cx -= carry ? CX : 0;
-            cy += sy + carry;
-            carry = cy >= CY;
-            cy -= carry ? CY : 0;
-            cz += sz + carry;
+            cell_fill_axis<Real>(sm + sa + CS * p, NQS, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
+                                 a.bc[0][g], a.bc[1][g], a.bc[2][g], ax, a.K, bad, hit);
+            fi += df;
+            const int carry = fi >= F;
+            fi -= carry ? F : 0;
+            si += ds + carry;
         }
     }
     if (bad) atomicOr(a.flag, 1);
@@ -180,14 +184,12 @@ __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const Pa
 #pragma unroll 1
     for (int r = 0; r < FPT; ++r) {
         const int t2 = ty + ROWS * r;
-        const int bx = tx;
-        const int by = ax == 2 ? 0 : t2;
-        const int bz = ax == 2 ? t2 : 0;
-        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+        const int gx = x0 + tx, gy = y0 + (ax == 2 ? 0 : t2), gz = z0 + (ax == 2 ? t2 : 0);
         if (gx < nx && gy < ny && gz < nz) {
-            const int c0 = bx + CX * (by + CY * bz);   // stencil cell i-2
+            // stencil cell i-2 of the face: s = the face's position along the axis
+            const int c0 = ax == 0 ? tx + CS * t2 : t2 + CS * tx;
             Real Ff[7], s1, s2;
-            face_flux<Real, VAR>(sm + c0, NC, ST, a.K, Ff, s1, s2);
+            face_flux<Real, VAR>(sm + c0, NQS, 1, a.K, Ff, s1, s2);
             const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
             // lab components of the frame momentum flux (n, t1, t2)
             Real *const fn = ax == 0 ? a.F[1] : (ax == 1 ? a.F[2] : a.F[3]);
