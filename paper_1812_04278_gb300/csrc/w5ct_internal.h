@@ -25,8 +25,9 @@ struct SweepTuning;
 
 // Defaults measured on GB300 (FP32 at 256^3: 2 blocks/SM of 16-high tiles,
 // 1.6x faster than 1 block of 8-high tiles; 3 blocks/SM or 32-high y/z tiles
-// are slower.  FP64 at 128^3: FP64-pipe bound, within 1% for 8- or 16-high
-// tiles and 1 or 2 blocks/SM; 16-high on every axis is the fastest).
+// are slower.  FP64 at 256^3: FP64-pipe bound; 32-high tiles of 256 threads,
+// four faces per thread, are 1% faster than 16-high ones (shorter y/z cell
+// boxes per face), and 384- or 512-thread blocks are within 0.5%).
 #ifndef W5CT_F32_T2X
 #define W5CT_F32_T2X 16
 #endif
@@ -37,10 +38,10 @@ struct SweepTuning;
 #define W5CT_F32_MINB 2
 #endif
 #ifndef W5CT_F64_T2X
-#define W5CT_F64_T2X 16
+#define W5CT_F64_T2X 32
 #endif
 #ifndef W5CT_F64_T2YZ
-#define W5CT_F64_T2YZ 16
+#define W5CT_F64_T2YZ 32
 #endif
 #ifndef W5CT_F64_MINB
 #define W5CT_F64_MINB 1
@@ -88,7 +89,8 @@ struct SinglePatchSweep {
 };
 
 // Tile shapes of the batched sweeps (chosen per patch and axis by the
-// autotuner).  Variant 0 is SweepCfg's tile (32 lanes); the float path also
+// autotuner).  Variant 0 is SweepCfg's tile (32 lanes) in float and 32 x 16
+// in double (patches are 16 to 64 cells across); the float path also
 // has narrower tiles that waste fewer lanes on patches whose sizes are not
 // multiples of 32 or of 16: (BX, T2, faces per thread) = (16, 16, 1),
 // (8, 16, 1), (8, 8, 1).  Every variant keeps 128 registers per thread: min
@@ -97,9 +99,11 @@ constexpr int kMaxTileVariants = 4;
 
 template <int AX, typename Real, int V>
 struct TileV;
+constexpr int kBatchedF64T2 = 16;
 template <int AX, typename Real>
 struct TileV<AX, Real, 0> {
-    static constexpr int T2 = SweepCfg<AX, Real>::T2, BX = 32, FPT = T2 / 8, MINB = SweepCfg<AX, Real>::MINB;
+    static constexpr int T2 = sizeof(Real) == 8 ? kBatchedF64T2 : SweepCfg<AX, Real>::T2, BX = 32, FPT = T2 / 8,
+                         MINB = SweepCfg<AX, Real>::MINB;
 };
 template <int AX, typename Real>
 struct TileV<AX, Real, 1> {
@@ -124,7 +128,7 @@ template <typename Real>
 inline void tile_shape(int axis, int v, int &bx, int &t2) {
     if (v == 0) {
         bx = 32;
-        t2 = axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
+        t2 = sizeof(Real) == 8 ? kBatchedF64T2 : axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
     } else {
         bx = v == 1 ? 16 : 8;
         t2 = v == 3 ? 8 : 16;
@@ -232,6 +236,7 @@ cudaError_t prepare_sweep_axis() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<Real, double>::value) {
+        if ((e = SinglePatchSweep<AX, Real, VAR, 16, C::MINB, 2>::prepare()) != cudaSuccess) return e;
         if ((e = SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::prepare()) != cudaSuccess) return e;
         if ((e = SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::prepare()) != cudaSuccess) return e;
     }
@@ -302,12 +307,6 @@ cudaError_t persistent_grid_v(int tv, int &blocks) {
     return PersistentLaunch<Real, VAR, 0>::grid(blocks);
 }
 
-// tile heights of the single-patch sweep along each axis for this type
-template <typename Real>
-inline int sweep_t2(int axis) {
-    return axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
-}
-
 template <int AX, typename Real, int VAR>
 cudaError_t launch_sweep_batched_axis(int tv, const SweepArgs<Real> &a, const PatchGeom *pgs, const int4 *tiles,
                                       int ntiles, cudaStream_t s) {
@@ -334,10 +333,10 @@ cudaError_t launch_sweep_batched_impl(int axis, int variant, int tv, const Sweep
 }
 
 // The FP64 sweep keeps one block of 256 threads per SM (its registers), so a
-// small patch fills the GPU only with shorter tiles: 8 high (256 threads, one
-// face each) or 4 high (128 threads, two blocks per SM).  The float sweep
-// always uses its default tile.
-constexpr int kSmallTileHeights[2] = {8, 4};
+// small patch fills the GPU only with shorter tiles: 16 high (256 threads, two
+// faces each), 8 high (one face each) or 4 high (128 threads, two blocks per
+// SM).  The float sweep always uses its default tile.
+constexpr int kSmallTileHeights[3] = {16, 8, 4};
 
 // blocks of the single-patch sweep along `axis` in tiles t2 high
 inline long long sweep_blocks(int axis, int t2, int nx, int ny, int nz) {
@@ -356,13 +355,14 @@ inline int choose_sweep_t2(int axis, int nx, int ny, int nz, int sms) {
     if (sweep_blocks(axis, t2d, nx, ny, nz) >= 2LL * sms) return t2d;
     for (int h : kSmallTileHeights)
         if (sweep_blocks(axis, h, nx, ny, nz) >= 2LL * sms) return h;
-    return kSmallTileHeights[1];
+    return kSmallTileHeights[2];
 }
 
 template <int AX, typename Real, int VAR>
 cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) {
     using C = SweepCfg<AX, Real>;
     if constexpr (std::is_same<Real, double>::value) {
+        if (t2 == 16 && C::T2 != 16) return SinglePatchSweep<AX, Real, VAR, 16, C::MINB, 2>::launch(a, s);
         if (t2 == 8) return SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::launch(a, s);
         if (t2 == 4) return SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::launch(a, s);
     }

@@ -38,6 +38,9 @@ struct SweepArgs {
     unsigned long long *hits;
 };
 
+// Cells whose loads a thread issues together when it stages a cell box.
+constexpr int kStageBatch = 3;
+
 // Tile of one block: BX lanes along x (coalesced loads and stores; every
 // tile has x fastest), T2 faces or pencils in the second direction, each
 // thread computing FPT of them (the block is BX x T2/FPT threads).
@@ -84,16 +87,38 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
     const int ox = x0 - (AX == 0 ? 2 : 0), oy = y0 - (AX == 1 ? 2 : 0), oz = z0 - (AX == 2 ? 2 : 0);
     const int tid = tx + TT::BX * ty;
 
-    // phase 1: per-cell primitives, flux and speeds of the cell box
+    // phase 1: per-cell primitives, flux and speeds of the cell box.  A
+    // thread issues the loads of up to kStageBatch of its cells before it
+    // fills any of them, so that the box costs one memory latency per batch
+    // rather than one per cell.
     bool bad = false, hit = false;
-    for (int c = tid; c < TT::NC; c += TT::NT) {
-        const int cx = c % TT::CX;
-        const int cy = (c / TT::CX) % TT::CY;
-        const int cz = c / (TT::CX * TT::CY);
-        const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
-        const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
-        cell_fill<Real, AX>(sm + c, TT::NC, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
-                            a.bc[0][g], a.bc[1][g], a.bc[2][g], a.K, bad, hit);
+    constexpr int NIT = (TT::NC + TT::NT - 1) / TT::NT;
+    constexpr int B = NIT < kStageBatch ? NIT : kStageBatch;
+#pragma unroll
+    for (int it0 = 0; it0 < NIT; it0 += B) {
+        Real v[B][8];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int c = tid + (it0 + j) * TT::NT;
+            if (it0 + j < NIT && c < TT::NC) {
+                const int cx = c % TT::CX;
+                const int cy = (c / TT::CX) % TT::CY;
+                const int cz = c / (TT::CX * TT::CY);
+                const int gx = wrapi(ox + cx, nx), gy = wrapi(oy + cy, ny), gz = wrapi(oz + cz, nz);
+                const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+#pragma unroll
+                for (int f = 0; f < 5; ++f) v[j][f] = a.q[f][g];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) v[j][5 + f] = a.bc[f][g];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int c = tid + (it0 + j) * TT::NT;
+            if (it0 + j < NIT && c < TT::NC)
+                cell_fill<Real, AX>(sm + c, TT::NC, v[j][0], v[j][1], v[j][2], v[j][3], v[j][4], v[j][5], v[j][6],
+                                    v[j][7], a.K, bad, hit);
+        }
     }
     if (bad) atomicOr(a.flag, 1);
     if (a.K.floors) {
@@ -154,23 +179,40 @@ __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const Pa
     // phase 1: per-cell quantities of the cell box, traversed x fastest
     // (coalesced loads): the x-sweep's fastest box index is s, the y- and
     // z-sweeps' is p; stepped by NT with a carry (no division per cell)
+    // (loads of kStageBatch cells issued before any of them is filled)
     bool bad = false, hit = false;
     {
         const int F = ax == 0 ? CS : NPC;
         int fi = tid % F, si = tid / F;
         const int df = NT % F, ds = NT / F;
-        for (int c = tid; c < NCELL; c += NT) {
-            const int sa = ax == 0 ? fi : si, p = ax == 0 ? si : fi;
-            const int gx = wrapi(ax == 0 ? x0 - 2 + sa : x0 + p, nx);
-            const int gy = wrapi(ax == 1 ? y0 - 2 + sa : (ax == 0 ? y0 + p : y0), ny);
-            const int gz = wrapi(ax == 2 ? z0 - 2 + sa : z0, nz);
-            const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
-            cell_fill_axis<Real>(sm + sa + CS * p, NQS, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
-                                 a.bc[0][g], a.bc[1][g], a.bc[2][g], ax, a.K, bad, hit);
-            fi += df;
-            const int carry = fi >= F;
-            fi -= carry ? F : 0;
-            si += ds + carry;
+        for (int c0 = tid; c0 < NCELL; c0 += kStageBatch * NT) {
+            Real v[kStageBatch][8];
+            int dst[kStageBatch];
+#pragma unroll
+            for (int j = 0; j < kStageBatch; ++j) {
+                dst[j] = -1;
+                if (c0 + j * NT < NCELL) {
+                    const int sa = ax == 0 ? fi : si, p = ax == 0 ? si : fi;
+                    const int gx = wrapi(ax == 0 ? x0 - 2 + sa : x0 + p, nx);
+                    const int gy = wrapi(ax == 1 ? y0 - 2 + sa : (ax == 0 ? y0 + p : y0), ny);
+                    const int gz = wrapi(ax == 2 ? z0 - 2 + sa : z0, nz);
+                    const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+#pragma unroll
+                    for (int f = 0; f < 5; ++f) v[j][f] = a.q[f][g];
+#pragma unroll
+                    for (int f = 0; f < 3; ++f) v[j][5 + f] = a.bc[f][g];
+                    dst[j] = sa + CS * p;
+                }
+                fi += df;
+                const int carry = fi >= F;
+                fi -= carry ? F : 0;
+                si += ds + carry;
+            }
+#pragma unroll
+            for (int j = 0; j < kStageBatch; ++j)
+                if (dst[j] >= 0)
+                    cell_fill_axis<Real>(sm + dst[j], NQS, v[j][0], v[j][1], v[j][2], v[j][3], v[j][4], v[j][5],
+                                         v[j][6], v[j][7], ax, a.K, bad, hit);
         }
     }
     if (bad) atomicOr(a.flag, 1);
