@@ -194,11 +194,11 @@ __global__ void __launch_bounds__(PersistentSweep<Real, VAR, V>::NT, PersistentS
         const int ax = t.x >> kItemAxisShift;
         const PatchGeom pg = pgs[t.x & kItemPatchMask];
         if (ax == 0)
-            sweep_tile<0, Real, VAR, P::C0::T2, P::BX, P::C0::FPT>(a0, pg, t.y, t.z, t.w, sm);
+            sweep_tile<0, Real, VAR, P::C0::T2, P::BX, P::C0::FPT, 1>(a0, pg, t.y, t.z, t.w, sm);
         else if (ax == 1)
-            sweep_tile<1, Real, VAR, P::C1::T2, P::BX, P::C1::FPT>(a1, pg, t.y, t.z, t.w, sm);
+            sweep_tile<1, Real, VAR, P::C1::T2, P::BX, P::C1::FPT, 1>(a1, pg, t.y, t.z, t.w, sm);
         else
-            sweep_tile<2, Real, VAR, P::C2::T2, P::BX, P::C2::FPT>(a2, pg, t.y, t.z, t.w, sm);
+            sweep_tile<2, Real, VAR, P::C2::T2, P::BX, P::C2::FPT, 1>(a2, pg, t.y, t.z, t.w, sm);
         __syncthreads();                   // shared memory and s_item are reused
     }
 }

@@ -38,7 +38,9 @@ struct SweepArgs {
     unsigned long long *hits;
 };
 
-// Cells whose loads a thread issues together when it stages a cell box.
+// Cells whose loads a thread of a single-axis sweep kernel issues together
+// when it stages a cell box (kernels that inline several sweeps stage one
+// cell at a time: their larger code measured slower with the batch).
 constexpr int kStageBatch = 3;
 
 // Tile of one block: BX lanes along x (coalesced loads and stores; every
@@ -76,8 +78,9 @@ struct PatchGeom {
 
 // One sweep tile (tile indices tbx, tby, tbz) of the patch described by g,
 // computed by the block's NT threads, numbered (tx, ty) in [0, BX) x
-// [0, ROWS).  sm: shared memory of NCQ * NC elements.
-template <int AX, typename Real, int VAR, int T2, int BX, int FPT>
+// [0, ROWS).  sm: shared memory of NCQ * NC elements.  SB: cells whose loads
+// a thread issues together when it stages the cell box.
+template <int AX, typename Real, int VAR, int T2, int BX, int FPT, int SB = kStageBatch>
 __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
                                               Real *sm, int tx, int ty) {
     using TT = SweepTile<AX, T2, BX, FPT>;
@@ -88,12 +91,12 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
     const int tid = tx + TT::BX * ty;
 
     // phase 1: per-cell primitives, flux and speeds of the cell box.  A
-    // thread issues the loads of up to kStageBatch of its cells before it
-    // fills any of them, so that the box costs one memory latency per batch
-    // rather than one per cell.
+    // thread issues the loads of up to SB of its cells before it fills any
+    // of them, so that the box costs one memory latency per batch rather
+    // than one per cell.
     bool bad = false, hit = false;
     constexpr int NIT = (TT::NC + TT::NT - 1) / TT::NT;
-    constexpr int B = NIT < kStageBatch ? NIT : kStageBatch;
+    constexpr int B = NIT < SB ? NIT : SB;
 #pragma unroll
     for (int it0 = 0; it0 < NIT; it0 += B) {
         Real v[B][8];
@@ -179,40 +182,23 @@ __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const Pa
     // phase 1: per-cell quantities of the cell box, traversed x fastest
     // (coalesced loads): the x-sweep's fastest box index is s, the y- and
     // z-sweeps' is p; stepped by NT with a carry (no division per cell)
-    // (loads of kStageBatch cells issued before any of them is filled)
     bool bad = false, hit = false;
     {
         const int F = ax == 0 ? CS : NPC;
         int fi = tid % F, si = tid / F;
         const int df = NT % F, ds = NT / F;
-        for (int c0 = tid; c0 < NCELL; c0 += kStageBatch * NT) {
-            Real v[kStageBatch][8];
-            int dst[kStageBatch];
-#pragma unroll
-            for (int j = 0; j < kStageBatch; ++j) {
-                dst[j] = -1;
-                if (c0 + j * NT < NCELL) {
-                    const int sa = ax == 0 ? fi : si, p = ax == 0 ? si : fi;
-                    const int gx = wrapi(ax == 0 ? x0 - 2 + sa : x0 + p, nx);
-                    const int gy = wrapi(ax == 1 ? y0 - 2 + sa : (ax == 0 ? y0 + p : y0), ny);
-                    const int gz = wrapi(ax == 2 ? z0 - 2 + sa : z0, nz);
-                    const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
-#pragma unroll
-                    for (int f = 0; f < 5; ++f) v[j][f] = a.q[f][g];
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) v[j][5 + f] = a.bc[f][g];
-                    dst[j] = sa + CS * p;
-                }
-                fi += df;
-                const int carry = fi >= F;
-                fi -= carry ? F : 0;
-                si += ds + carry;
-            }
-#pragma unroll
-            for (int j = 0; j < kStageBatch; ++j)
-                if (dst[j] >= 0)
-                    cell_fill_axis<Real>(sm + dst[j], NQS, v[j][0], v[j][1], v[j][2], v[j][3], v[j][4], v[j][5],
-                                         v[j][6], v[j][7], ax, a.K, bad, hit);
+        for (int c = tid; c < NCELL; c += NT) {
+            const int sa = ax == 0 ? fi : si, p = ax == 0 ? si : fi;
+            const int gx = wrapi(ax == 0 ? x0 - 2 + sa : x0 + p, nx);
+            const int gy = wrapi(ax == 1 ? y0 - 2 + sa : (ax == 0 ? y0 + p : y0), ny);
+            const int gz = wrapi(ax == 2 ? z0 - 2 + sa : z0, nz);
+            const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
+            cell_fill_axis<Real>(sm + sa + CS * p, NQS, a.q[0][g], a.q[1][g], a.q[2][g], a.q[3][g], a.q[4][g],
+                                 a.bc[0][g], a.bc[1][g], a.bc[2][g], ax, a.K, bad, hit);
+            fi += df;
+            const int carry = fi >= F;
+            fi -= carry ? F : 0;
+            si += ds + carry;
         }
     }
     if (bad) atomicOr(a.flag, 1);
@@ -249,10 +235,10 @@ __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const Pa
 }
 
 // One tile computed by the whole block, blockDim = (BX, ROWS).
-template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8>
+template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8, int SB = kStageBatch>
 __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
                                            Real *sm) {
-    sweep_tile_at<AX, Real, VAR, T2, BX, FPT>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
+    sweep_tile_at<AX, Real, VAR, T2, BX, FPT, SB>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
 }
 
 // One tile per block over a single patch: 32 x T2 / FPT threads (at most
