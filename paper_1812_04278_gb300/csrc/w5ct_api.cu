@@ -284,7 +284,7 @@ int launch_cellb(w5ct_ctx *c) {
             c->pg_dev, c->cells_dev, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
             plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
     } else {
-        cellb_kernel<Real><<<cell_grid(c), dim3(32, 8), 0, c->stream>>>(
+        cellb_kernel<Real><<<cellb_grid(c->nx, c->ny, c->nz), dim3(32, 8), 0, c->stream>>>(
             c->nx, c->ny, c->nz, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
             plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
     }
@@ -956,10 +956,9 @@ int w5ct_get_state(w5ct_ctx *c, int patch, double *cons, double *bface, double *
             W5_CUDA(c, cudaMemcpyAsync(bface + f * np, c->b0 + f * n + off, np * 8, kind, c->stream));
     if (bcell) {
         // the FP64 accumulator planes are free between steps
-        const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
-        cellb_kernel<double><<<grid, dim3(32, 8), 0, c->stream>>>(g.nx, g.ny, g.nz, c->b0 + off, c->b0 + n + off,
-                                                                  c->b0 + 2 * n + off, c->acc + off, c->acc + n + off,
-                                                                  c->acc + 2 * n + off);
+        cellb_kernel<double><<<cellb_grid(g.nx, g.ny, g.nz), dim3(32, 8), 0, c->stream>>>(
+            g.nx, g.ny, g.nz, c->b0 + off, c->b0 + n + off, c->b0 + 2 * n + off, c->acc + off, c->acc + n + off,
+            c->acc + 2 * n + off);
         c->launches++;
         W5_CUDA(c, cudaGetLastError());
         for (int f = 0; f < 3; ++f)
@@ -1311,9 +1310,9 @@ int adjoint_step_impl(w5ct_ctx *c, double dt, const double *lq_fin, const double
         adj_flux_kernel<<<nb, 256, 0, st>>>(g, lamD, lamO, lamF, lamS);
         // the stage's cell field from its stored face field
         const Real *sq = stage + (size_t)s * 8 * n, *sb = sq + 5 * n;
-        cellb_kernel<Real><<<cell_grid(c), dim3(32, 8), 0, st>>>(c->nx, c->ny, c->nz, sb, sb + n, sb + 2 * n,
-                                                                 plane<Real>(c->bc, nl, 0), plane<Real>(c->bc, nl, 1),
-                                                                 plane<Real>(c->bc, nl, 2));
+        cellb_kernel<Real><<<cellb_grid(c->nx, c->ny, c->nz), dim3(32, 8), 0, st>>>(
+            c->nx, c->ny, c->nz, sb, sb + n, sb + 2 * n, plane<Real>(c->bc, nl, 0), plane<Real>(c->bc, nl, 1),
+            plane<Real>(c->bc, nl, 2));
         W5_CUDA(c, cudaMemsetAsync(cur, 0, 5 * n * 8, st));
         W5_CUDA(c, cudaMemsetAsync(lamBc, 0, 3 * n * 8, st));
         for (int ax = 0; ax < 3; ++ax) {
