@@ -51,6 +51,13 @@ FACE_FLOPS = {0: 2760, 1: 2858}
 CT_FLUX_FLOPS = 10
 SWEEP_FLOPS_PER_ZONE = {v: CELL_FLOPS + FACE_FLOPS[v] + CT_FLUX_FLOPS for v in (0, 1)}
 STEP_FLOPS_PER_ZONE = {0: 34881, 1: 36057}
+# The vector-Jacobian product of one step, per zone: the step's forward
+# operations (its stages recomputed once) plus the reverse-mode operations of
+# differentiating it with respect to its input state, counted by the same
+# program operation by operation (each partial contribution costs its
+# multiplications / divisions plus one accumulating addition; operations on
+# values that do not depend on the state cost nothing in reverse).
+ADJOINT_STEP_FLOPS_PER_ZONE = {0: 129072, 1: 132768}
 # Peaks: FP32 from the unit counts (152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz);
 # FP64 from the published GB300 rate (1.25 TFLOP/s); measured copy bandwidth.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -993,6 +1000,15 @@ def adjoint_record(args, compact=False):
                "adjoint_ms_per_step": ms_b / args.steps, "forward_ms_per_step": ms_f / args.steps,
                "one_adjoint_step_ms": ms_adj_step,
                "adjoint_zone_steps_per_s": zones * args.steps / (ms_b * 1e-3)}
+        # roofline of the whole adjoint step (every kernel of the backward
+        # pass) on the algorithmic count of a vector-Jacobian product
+        ach = ADJOINT_STEP_FLOPS_PER_ZONE[1] * zones / (ms_b / args.steps * 1e-3) / 1e12
+        pk = PEAK_FP64_TFLOPS if name == "fp64" else PEAK_FP32_TFLOPS
+        rec["roofline"] = {"kernel": "one adjoint step (all kernels of the backward pass)", "bound": "alu",
+                           "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
+                           "algorithmic_flops_per_zone": ADJOINT_STEP_FLOPS_PER_ZONE[1],
+                           "peak_source": "GB300 FP64 published rate" if name == "fp64"
+                           else "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
         if name == "fp64" and compact:
             st = solver(prec)
             _, gt, _, _ = grad(st, pbt, dt)
@@ -1034,6 +1050,7 @@ def adjoint_record(args, compact=False):
                             f"per step", "value": value, "unit": "adjoint zone-steps/s",
                 "fp64_adjoint_ms_per_step": out["fp64"]["adjoint_ms_per_step"],
                 "fp64_forward_ms_per_step": out["fp64"]["forward_ms_per_step"],
+                "fp64_roofline": out["fp64"]["roofline"], "fp32_bulk_roofline_frac": out["fp32_bulk"]["roofline"]["frac"],
                 "fp32_bulk_value": out["fp32_bulk"]["adjoint_zone_steps_per_s"],
                 "fp32_bulk_adjoint_ms_per_step": out["fp32_bulk"]["adjoint_ms_per_step"],
                 "fd_check_textured_rel_err": out["fp64"]["fd_check_textured"]["rel_err"],
@@ -1048,6 +1065,7 @@ def adjoint_record(args, compact=False):
                                f"radius 0.1); misfit to the wave without the overpressure after {args.steps} steps "
                                f"of fixed dt (CFL 0.8 of the initial state); gradient in rho, v and the edge vector "
                                f"potential; WENO-Z; one checkpoint per step", "zones": zones, "grid": [n, n, n]},
+        "roofline": out["fp64"]["roofline"],
         "fp64": out["fp64"], "fp32_bulk": out["fp32_bulk"], "fp32_vs_fp64_grad_max_rel": rel32,
         "fp32_vs_fp64_directional_rel": abs(gd32 - gd64) / abs(gd64),
         "kernel_src": kernel_source_hash(),

@@ -21,8 +21,27 @@
 //   div    operations of one cell's flux divergence in one sweep;
 //   step   operations per zone of one whole RK4 + CT step (ora_step), and
 //   sweep  the per-zone total of one sweep (cell + face + div),
+//   step_reverse  operations per zone of the reverse sweep of one step in
+//          reverse-mode differentiation with respect to the step's input
+//          state (q^n, b^n), dt held fixed, and
+//   adjoint_step  step + step_reverse: the vector-Jacobian product of one
+//          step, its forward stages recomputed once,
 // measured on a generic smooth state of 12 x 10 x 8 cells (every field
 // varies, no degenerate branch is taken).
+//
+// Reverse-mode counts (Griewank's operation-by-operation rule, with an
+// activity analysis: a value is active when it depends on the input state;
+// operations on passive values cost nothing in reverse).  For c = f(a, b),
+// each active operand's adjoint receives one contribution, and every
+// contribution costs its multiplications and divisions plus the one
+// addition that accumulates it:
+//   c = a +- b     1 per active operand
+//   c = a * b      2 per active operand (c_bar * b, accumulate)
+//   c = a / b      t = c_bar / b once, a_bar += t (1), b_bar -= t c (2):
+//                  4 with both active, 2 with a only, 3 with b only
+//   c = sqrt(a)    3 (c_bar / c, times 1/2, accumulate)
+//   c = -a, |a|    1 (signed accumulation)
+// Selections (max, branches) copy a value and cost 0 either way.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -30,32 +49,45 @@
 
 #include <cmath>
 
-static long long g_ops = 0;
+static long long g_ops = 0;   // forward operations
+static long long g_rev = 0;   // reverse-mode operations (see above)
+
+static inline long long rev_div(bool a, bool b) { return (a && b) ? 4 : a ? 2 : b ? 3 : 0; }
 
 struct Flop {
     double v;
+    bool act;   // depends on the input state
     Flop() = default;
-    constexpr Flop(double x) : v(x) {}
+    constexpr Flop(double x) : v(x), act(false) {}
+    constexpr Flop(double x, bool a) : v(x), act(a) {}
     explicit operator int() const { return (int)v; }
     explicit operator long() const { return (long)v; }
-    Flop &operator+=(Flop o) { ++g_ops; v += o.v; return *this; }
-    Flop &operator-=(Flop o) { ++g_ops; v -= o.v; return *this; }
-    Flop &operator*=(Flop o) { ++g_ops; v *= o.v; return *this; }
-    Flop &operator/=(Flop o) { ++g_ops; v /= o.v; return *this; }
+    Flop &operator+=(Flop o) { ++g_ops; g_rev += act + o.act; v += o.v; act = act || o.act; return *this; }
+    Flop &operator-=(Flop o) { ++g_ops; g_rev += act + o.act; v -= o.v; act = act || o.act; return *this; }
+    Flop &operator*=(Flop o) { ++g_ops; g_rev += 2 * (act + o.act); v *= o.v; act = act || o.act; return *this; }
+    Flop &operator/=(Flop o) { ++g_ops; g_rev += rev_div(act, o.act); v /= o.v; act = act || o.act; return *this; }
 };
-static inline Flop operator+(Flop a, Flop b) { ++g_ops; return Flop(a.v + b.v); }
-static inline Flop operator-(Flop a, Flop b) { ++g_ops; return Flop(a.v - b.v); }
-static inline Flop operator*(Flop a, Flop b) { ++g_ops; return Flop(a.v * b.v); }
-static inline Flop operator/(Flop a, Flop b) { ++g_ops; return Flop(a.v / b.v); }
-static inline Flop operator-(Flop a) { return Flop(-a.v); }
+static inline Flop operator+(Flop a, Flop b) { ++g_ops; g_rev += a.act + b.act; return Flop(a.v + b.v, a.act || b.act); }
+static inline Flop operator-(Flop a, Flop b) { ++g_ops; g_rev += a.act + b.act; return Flop(a.v - b.v, a.act || b.act); }
+static inline Flop operator*(Flop a, Flop b) {
+    ++g_ops;
+    g_rev += 2 * (a.act + b.act);
+    return Flop(a.v * b.v, a.act || b.act);
+}
+static inline Flop operator/(Flop a, Flop b) {
+    ++g_ops;
+    g_rev += rev_div(a.act, b.act);
+    return Flop(a.v / b.v, a.act || b.act);
+}
+static inline Flop operator-(Flop a) { g_rev += a.act; return Flop(-a.v, a.act); }
 static inline bool operator<(Flop a, Flop b) { return a.v < b.v; }
 static inline bool operator>(Flop a, Flop b) { return a.v > b.v; }
 static inline bool operator<=(Flop a, Flop b) { return a.v <= b.v; }
 static inline bool operator>=(Flop a, Flop b) { return a.v >= b.v; }
 static inline bool operator==(Flop a, Flop b) { return a.v == b.v; }
 static inline bool operator!=(Flop a, Flop b) { return a.v != b.v; }
-static inline Flop sqrt(Flop a) { ++g_ops; return Flop(std::sqrt(a.v)); }
-static inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
+static inline Flop sqrt(Flop a) { ++g_ops; g_rev += a.act ? 3 : 0; return Flop(std::sqrt(a.v), a.act); }
+static inline Flop fabs(Flop a) { g_rev += a.act; return Flop(std::fabs(a.v), a.act); }
 static inline bool isfinite(Flop a) { return std::isfinite(a.v); }
 
 #define double Flop
@@ -106,8 +138,8 @@ int main(int argc, char **argv) {
     double *cons = (double *)malloc(sizeof(double) * 5 * n), *bface = (double *)malloc(sizeof(double) * 3 * n);
     generic_state(nx, ny, nz, cons, bface);
     Flop *cf = (Flop *)malloc(sizeof(Flop) * 5 * n), *bf = (Flop *)malloc(sizeof(Flop) * 3 * n);
-    for (long p = 0; p < 5 * n; p++) cf[p] = Flop(cons[p]);
-    for (long p = 0; p < 3 * n; p++) bf[p] = Flop(bface[p]);
+    for (long p = 0; p < 5 * n; p++) cf[p] = Flop(cons[p], true);
+    for (long p = 0; p < 3 * n; p++) bf[p] = Flop(bface[p], true);
     if (ora_set_state(c, cf, bf) != ORA_OK) return 1;
 
     // per-cell recovery and per-face flux along x, counted call by call
@@ -141,21 +173,25 @@ int main(int argc, char **argv) {
     sweep(c, 0, c->q, Bc, D, S[0], S[1]);
     const long long sweep_ops = g_ops - t0;
 
-    // one whole RK4 + CT step
+    // one whole RK4 + CT step, from the active input state (dt passive)
+    if (ora_set_state(c, cf, bf) != ORA_OK) return 1;
     t0 = g_ops;
+    const long long r0 = g_rev;
     if (ora_step(c, Flop(1e-3)) != ORA_OK) return 1;
-    const long long step_ops = g_ops - t0;
+    const long long step_ops = g_ops - t0, step_rev = g_rev - r0;
     if (bad || hits) return 1;
 
     const double per_cell = (double)cell_ops / n, per_face_core = (double)face_core_ops / n;
     const double per_sweep = (double)sweep_ops / n, per_step = (double)step_ops / n;
+    const double per_step_rev = (double)step_rev / n;
     // the divergence: three operations per conserved field (difference,
     // division by the spacing, accumulation)
     const double per_div = 15.0;
     const double per_face = per_sweep - per_cell - per_div;
     printf("{\"variant\": %d, \"cell\": %.4f, \"face_core\": %.4f, \"face\": %.4f, \"div\": %.4f, "
-           "\"sweep\": %.4f, \"step\": %.4f}\n",
-           variant, per_cell, per_face_core, per_face, per_div, per_sweep, per_step);
+           "\"sweep\": %.4f, \"step\": %.4f, \"step_reverse\": %.4f, \"adjoint_step\": %.4f}\n",
+           variant, per_cell, per_face_core, per_face, per_div, per_sweep, per_step, per_step_rev,
+           per_step + per_step_rev);
     free_planes(Bc, 3);
     free_planes(D, 5);
     free_planes(S, 2);

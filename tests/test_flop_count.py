@@ -38,6 +38,18 @@ def test_bench_flop_constants_equal_the_oracle_counts(counts, variant):
     assert c["sweep"] == bench.SWEEP_FLOPS_PER_ZONE[variant] + c["div"]
     assert round(c["step"]) == bench.STEP_FLOPS_PER_ZONE[variant]
     assert abs(c["step"] - round(c["step"])) < 0.01
+    assert round(c["adjoint_step"]) == bench.ADJOINT_STEP_FLOPS_PER_ZONE[variant]
+
+
+def test_reverse_mode_count_is_a_few_forward_counts(counts):
+    """The reverse sweep of a step costs between one and four times its
+    forward operations (the bound of reverse-mode differentiation for
+    +, -, * and /: at most two multiplications and two additions per
+    operand contribution)."""
+    for variant in (0, 1):
+        c = counts[variant]
+        assert c["step"] < c["step_reverse"] < 4 * c["step"], (variant, c)
+        assert c["adjoint_step"] == pytest.approx(c["step"] + c["step_reverse"])
 
 
 def test_step_count_is_four_stages_of_three_sweeps_plus_ct(counts):
