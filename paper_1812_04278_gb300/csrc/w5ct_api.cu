@@ -285,8 +285,9 @@ int launch_cellb(w5ct_ctx *c) {
             plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
     } else {
         cellb_kernel<Real><<<cellb_grid(c->nx, c->ny, c->nz), dim3(32, 8), 0, c->stream>>>(
-            c->nx, c->ny, c->nz, plane<Real>(c->bs, n, 0), plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2),
-            plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1), plane<Real>(c->bc, n, 2));
+            c->nx, c->ny, c->nz, cellb_chunk(c->nx, c->ny, c->nz), plane<Real>(c->bs, n, 0),
+            plane<Real>(c->bs, n, 1), plane<Real>(c->bs, n, 2), plane<Real>(c->bc, n, 0), plane<Real>(c->bc, n, 1),
+            plane<Real>(c->bc, n, 2));
     }
     c->launches++;
     W5_CUDA(c, cudaGetLastError());
@@ -957,8 +958,8 @@ int w5ct_get_state(w5ct_ctx *c, int patch, double *cons, double *bface, double *
     if (bcell) {
         // the FP64 accumulator planes are free between steps
         cellb_kernel<double><<<cellb_grid(g.nx, g.ny, g.nz), dim3(32, 8), 0, c->stream>>>(
-            g.nx, g.ny, g.nz, c->b0 + off, c->b0 + n + off, c->b0 + 2 * n + off, c->acc + off, c->acc + n + off,
-            c->acc + 2 * n + off);
+            g.nx, g.ny, g.nz, cellb_chunk(g.nx, g.ny, g.nz), c->b0 + off, c->b0 + n + off, c->b0 + 2 * n + off,
+            c->acc + off, c->acc + n + off, c->acc + 2 * n + off);
         c->launches++;
         W5_CUDA(c, cudaGetLastError());
         for (int f = 0; f < 3; ++f)
@@ -1311,8 +1312,8 @@ int adjoint_step_impl(w5ct_ctx *c, double dt, const double *lq_fin, const double
         // the stage's cell field from its stored face field
         const Real *sq = stage + (size_t)s * 8 * n, *sb = sq + 5 * n;
         cellb_kernel<Real><<<cellb_grid(c->nx, c->ny, c->nz), dim3(32, 8), 0, st>>>(
-            c->nx, c->ny, c->nz, sb, sb + n, sb + 2 * n, plane<Real>(c->bc, nl, 0), plane<Real>(c->bc, nl, 1),
-            plane<Real>(c->bc, nl, 2));
+            c->nx, c->ny, c->nz, cellb_chunk(c->nx, c->ny, c->nz), sb, sb + n, sb + 2 * n,
+            plane<Real>(c->bc, nl, 0), plane<Real>(c->bc, nl, 1), plane<Real>(c->bc, nl, 2));
         W5_CUDA(c, cudaMemsetAsync(cur, 0, 5 * n * 8, st));
         W5_CUDA(c, cudaMemsetAsync(lamBc, 0, 3 * n * 8, st));
         for (int ax = 0; ax < 3; ++ax) {

@@ -226,21 +226,26 @@ template <typename Real, int VAR>
 __global__ void __launch_bounds__(FusedBlock<Real>::NT, FusedBlock<Real>::MINB) fused_step_kernel(FusedArgs<Real> A) {
     constexpr int NT = FusedBlock<Real>::NT;
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
-    __shared__ int s_item, s_ok;
+    __shared__ int s_item, s_ok, s_next;
+    __shared__ const int *s_seen[2];              // thread 0: counters seen complete
     __shared__ double s_red[3 * 32];
     Real *sm = reinterpret_cast<Real *>(w5ct_smem);
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const FusedCounters &C = A.ctr;
-    const int *seen[2] = {nullptr, nullptr};    // thread 0: counters seen complete
-    int next = 0;
-    if (tid == 0) next = atomicAdd(C.queue, 1);
+    // thread 0's queue state lives in shared memory, not in registers that
+    // every thread would carry through the sweep arithmetic
+    if (tid == 0) {
+        s_seen[0] = nullptr;
+        s_seen[1] = nullptr;
+        s_next = atomicAdd(C.queue, 1);
+    }
     for (;;) {
-        if (tid == 0) s_item = next;
+        if (tid == 0) s_item = s_next;
         __syncthreads();
         const int it = s_item;
         if (it >= A.nitems) break;
         // the following item, fetched while this one runs
-        if (tid == 0) next = atomicAdd(C.queue, 1);
+        if (tid == 0) s_next = atomicAdd(C.queue, 1);
         const int4 t = A.items[it];
         const int p = t.x;
         const int type = t.y & 7, stage = (t.y >> 3) & 3, axis = (t.y >> 5) & 3, v = t.y >> 8;
@@ -250,16 +255,16 @@ __global__ void __launch_bounds__(FusedBlock<Real>::NT, FusedBlock<Real>::MINB) 
             bool ok = true;
             switch (type) {
                 case FI_CELLB:
-                    if (stage > 0) ok = fused_wait(C, C.update(stage - 1, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen);
+                    if (stage > 0) ok = fused_wait(C, C.update(stage - 1, p), A.ncb[p], A.spin_limit, A.a[0].flag, s_seen);
                     break;
-                case FI_SPEED: ok = fused_wait(C, C.cellb(0, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen); break;
-                case FI_DT: ok = fused_wait(C, C.speed(p), A.ncb[p], A.spin_limit, A.a[0].flag, seen); break;
+                case FI_SPEED: ok = fused_wait(C, C.cellb(0, p), A.ncb[p], A.spin_limit, A.a[0].flag, s_seen); break;
+                case FI_DT: ok = fused_wait(C, C.speed(p), A.ncb[p], A.spin_limit, A.a[0].flag, s_seen); break;
                 case FI_SWEEP:
-                    ok = fused_wait(C, C.cellb(stage, p), A.ncb[p], A.spin_limit, A.a[0].flag, seen);
+                    ok = fused_wait(C, C.cellb(stage, p), A.ncb[p], A.spin_limit, A.a[0].flag, s_seen);
                     break;
                 default:
-                    ok = fused_wait(C, C.sweep(stage, p), A.ntile[p], A.spin_limit, A.a[0].flag, seen);
-                    if (ok && stage == 0) ok = fused_wait(C, C.dtc(p), 1, A.spin_limit, A.a[0].flag, seen);
+                    ok = fused_wait(C, C.sweep(stage, p), A.ntile[p], A.spin_limit, A.a[0].flag, s_seen);
+                    if (ok && stage == 0) ok = fused_wait(C, C.dtc(p), 1, A.spin_limit, A.a[0].flag, s_seen);
                     break;
             }
             s_ok = ok ? 1 : 0;

@@ -293,20 +293,30 @@ __device__ __forceinline__ void cellb_cell(int nx, int ny, int nz, size_t off, i
 }
 
 // The cell field of one patch: a block of 32 x 8 (x, y) columns marches
-// along z over kCellbChunk planes, keeping the z-stencil's four b_z values in
+// along z over `chunk` planes, keeping the z-stencil's four b_z values in
 // registers (one new b_z load per cell; same arithmetic as cellb_cell).
-constexpr int kCellbChunk = 16;
+// The chunk is 16 planes, halved while the grid would have fewer than
+// kCellbMinBlocks blocks (small patches keep one block per 32 x 8 x 1 cells).
+constexpr int kCellbChunk = 16, kCellbMinBlocks = 1024;
+
+inline int cellb_chunk(int nx, int ny, int nz) {
+    const long long cols = (long long)((nx + 31) / 32) * ((ny + 7) / 8);
+    int chunk = kCellbChunk;
+    while (chunk > 1 && cols * ((nz + chunk - 1) / chunk) < kCellbMinBlocks) chunk /= 2;
+    return chunk;
+}
 
 inline dim3 cellb_grid(int nx, int ny, int nz) {
-    return dim3((nx + 31) / 32, (ny + 7) / 8, (nz + kCellbChunk - 1) / kCellbChunk);
+    const int chunk = cellb_chunk(nx, ny, nz);
+    return dim3((nx + 31) / 32, (ny + 7) / 8, (nz + chunk - 1) / chunk);
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, const Real *__restrict__ bx,
+__global__ void __launch_bounds__(256) cellb_kernel(int nx, int ny, int nz, int chunk, const Real *__restrict__ bx,
                                                     const Real *__restrict__ by, const Real *__restrict__ bz,
                                                     Real *__restrict__ Bx, Real *__restrict__ By, Real *__restrict__ Bz) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-    const int k0 = blockIdx.z * kCellbChunk, k1 = min(k0 + kCellbChunk, nz);
+    const int k0 = blockIdx.z * chunk, k1 = min(k0 + chunk, nz);
     if (i >= nx || j >= ny) return;
     const long long sy = nx, sz = (long long)nx * ny;
     const long long xm2 = wrapi(i - 2, nx) - i, xm1 = wrapi(i - 1, nx) - i, xp1 = wrapi(i + 1, nx) - i;
