@@ -25,9 +25,10 @@ struct SweepTuning;
 
 // Defaults measured on GB300 (FP32 at 256^3: 2 blocks/SM of 16-high tiles,
 // 1.6x faster than 1 block of 8-high tiles; 3 blocks/SM or 32-high y/z tiles
-// are slower.  FP64 at 256^3: FP64-pipe bound; 32-high tiles of 256 threads,
-// four faces per thread, are 1% faster than 16-high ones (shorter y/z cell
-// boxes per face), and 384- or 512-thread blocks are within 0.5%).
+// are slower.  FP64 at 256^3: FP64-pipe bound, one 256-thread block of
+// 16-high tiles per SM; its cell box with the forward differences (NBQ
+// planes) leaves no room for 32-high tiles, which without the differences
+// were 1% faster; 384- or 512-thread blocks measured within 0.5%).
 #ifndef W5CT_F32_T2X
 #define W5CT_F32_T2X 16
 #endif
@@ -38,10 +39,10 @@ struct SweepTuning;
 #define W5CT_F32_MINB 2
 #endif
 #ifndef W5CT_F64_T2X
-#define W5CT_F64_T2X 32
+#define W5CT_F64_T2X 16
 #endif
 #ifndef W5CT_F64_T2YZ
-#define W5CT_F64_T2YZ 32
+#define W5CT_F64_T2YZ 16
 #endif
 #ifndef W5CT_F64_MINB
 #define W5CT_F64_MINB 1
@@ -65,7 +66,7 @@ struct SweepCfg {
     static constexpr int MINB = SweepTuning<Real>::MINB;
     static constexpr int FPT = SweepTuning<Real>::FPT;
     using TT = SweepTile<AX, T2, 32, FPT>;
-    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
 };
 
 // Single-patch sweep in tiles of 32 x T2 faces, FPT per thread (the block
@@ -73,7 +74,7 @@ struct SweepCfg {
 template <int AX, typename Real, int VAR, int T2, int MINB, int FPT>
 struct SinglePatchSweep {
     using TT = SweepTile<AX, T2, 32, FPT>;
-    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
     static cudaError_t prepare() {
         return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -139,7 +140,7 @@ template <int AX, typename Real, int VAR, int V>
 struct BatchedSweep {
     using C = TileV<AX, Real, V>;
     using TT = SweepTile<AX, C::T2, C::BX, C::FPT>;
-    static constexpr size_t smem = (size_t)TT::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
     static cudaError_t prepare() {
         return cudaFuncSetAttribute(sweep_batched_kernel<AX, Real, VAR, C::T2, C::MINB, C::BX, C::FPT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -170,9 +171,9 @@ struct PersistentSweep {
     static_assert(T0::NT == T1::NT && T1::NT == T2_::NT && C0::BX == C1::BX && C1::BX == C2::BX,
                   "one block shape for the three axes");
     static constexpr int NT = T0::NT, BX = C0::BX, ROWS = T0::ROWS, MINB = C0::MINB;
-    static constexpr size_t smem0 = (size_t)T0::NC * NCQ * sizeof(Real);
-    static constexpr size_t smem1 = (size_t)T1::NC * NCQ * sizeof(Real);
-    static constexpr size_t smem2 = (size_t)T2_::NC * NCQ * sizeof(Real);
+    static constexpr size_t smem0 = (size_t)T0::NC * box_quantities<Real>() * sizeof(Real);
+    static constexpr size_t smem1 = (size_t)T1::NC * box_quantities<Real>() * sizeof(Real);
+    static constexpr size_t smem2 = (size_t)T2_::NC * box_quantities<Real>() * sizeof(Real);
     static constexpr size_t smem = smem0 > smem1 ? (smem0 > smem2 ? smem0 : smem2) : (smem1 > smem2 ? smem1 : smem2);
 };
 
@@ -236,7 +237,6 @@ cudaError_t prepare_sweep_axis() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<Real, double>::value) {
-        if ((e = SinglePatchSweep<AX, Real, VAR, 16, C::MINB, 2>::prepare()) != cudaSuccess) return e;
         if ((e = SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::prepare()) != cudaSuccess) return e;
         if ((e = SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::prepare()) != cudaSuccess) return e;
     }
@@ -333,10 +333,10 @@ cudaError_t launch_sweep_batched_impl(int axis, int variant, int tv, const Sweep
 }
 
 // The FP64 sweep keeps one block of 256 threads per SM (its registers), so a
-// small patch fills the GPU only with shorter tiles: 16 high (256 threads, two
-// faces each), 8 high (one face each) or 4 high (128 threads, two blocks per
-// SM).  The float sweep always uses its default tile.
-constexpr int kSmallTileHeights[3] = {16, 8, 4};
+// small patch fills the GPU only with shorter tiles: 8 high (256 threads, one
+// face each) or 4 high (128 threads, two blocks per SM).  The float sweep
+// always uses its default tile.
+constexpr int kSmallTileHeights[2] = {8, 4};
 
 // blocks of the single-patch sweep along `axis` in tiles t2 high
 inline long long sweep_blocks(int axis, int t2, int nx, int ny, int nz) {
@@ -347,25 +347,21 @@ inline long long sweep_blocks(int axis, int t2, int nx, int ny, int nz) {
 
 // Tile height of the single-patch sweep along `axis`: the default, or for
 // FP64 the tallest of the shorter tiles that gives every SM at least two
-// blocks (the shortest if none does).  The 32-high FP64 default needs at
-// least 32 blocks per SM: with fewer, the last partial wave of one-block-
-// per-SM launches costs more than the taller box saves (128^3: 6.73 ms
-// against 6.56 ms for 16-high tiles; 256^3: 51.9 against 52.4 ms).
+// blocks (the shortest if none does).
 template <typename Real>
 inline int choose_sweep_t2(int axis, int nx, int ny, int nz, int sms) {
     const int t2d = axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
     if (!std::is_same<Real, double>::value) return t2d;
-    if (sweep_blocks(axis, t2d, nx, ny, nz) >= 32LL * sms) return t2d;
+    if (sweep_blocks(axis, t2d, nx, ny, nz) >= 2LL * sms) return t2d;
     for (int h : kSmallTileHeights)
         if (sweep_blocks(axis, h, nx, ny, nz) >= 2LL * sms) return h;
-    return kSmallTileHeights[2];
+    return kSmallTileHeights[1];
 }
 
 template <int AX, typename Real, int VAR>
 cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) {
     using C = SweepCfg<AX, Real>;
     if constexpr (std::is_same<Real, double>::value) {
-        if (t2 == 16 && C::T2 != 16) return SinglePatchSweep<AX, Real, VAR, 16, C::MINB, 2>::launch(a, s);
         if (t2 == 8) return SinglePatchSweep<AX, Real, VAR, 8, C::MINB, 1>::launch(a, s);
         if (t2 == 4) return SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::launch(a, s);
     }

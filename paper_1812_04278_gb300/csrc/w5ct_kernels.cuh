@@ -78,7 +78,7 @@ struct PatchGeom {
 
 // One sweep tile (tile indices tbx, tby, tbz) of the patch described by g,
 // computed by the block's NT threads, numbered (tx, ty) in [0, BX) x
-// [0, ROWS).  sm: shared memory of NCQ * NC elements.  SB: cells whose loads
+// [0, ROWS).  sm: shared memory of box_quantities<Real>() * NC elements.  SB: cells whose loads
 // a thread issues together when it stages the cell box.
 template <int AX, typename Real, int VAR, int T2, int BX, int FPT, int SB = kStageBatch>
 __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
@@ -130,6 +130,28 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
     }
     __syncthreads();
 
+    // difference pass (FP64): the forward differences of F and u of every
+    // cell that has a successor along the sweep axis (the last one has none
+    // and no stencil needs it)
+    if constexpr (box_diff<Real>()) {
+        constexpr int NIT = (TT::NC + TT::NT - 1) / TT::NT;
+        constexpr int LAST = (AX == 0 ? TT::CX : AX == 1 ? TT::CY : TT::CZ) - 1;
+        CellDiff<Real> d[NIT];
+        bool has[NIT];
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            const int c = tid + it * TT::NT;
+            const int ca = AX == 0 ? c % TT::CX : AX == 1 ? (c / TT::CX) % TT::CY : c / (TT::CX * TT::CY);
+            has[it] = c < TT::NC && ca < LAST;
+            if (has[it]) box_diff_load<Real>(sm, TT::NC, c, TT::ST, d[it]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < NIT; ++it)
+            if (has[it]) box_diff_store<Real>(sm, TT::NC, tid + it * TT::NT, d[it]);
+        __syncthreads();
+    }
+
     // phase 2: FPT interfaces per thread
 #pragma unroll 1
     for (int r = 0; r < TT::FPT; ++r) {
@@ -141,7 +163,7 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
         if (gx < nx && gy < ny && gz < nz) {
             const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
             Real Ff[7], s1, s2;
-            face_flux<Real, VAR>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
+            face_flux<Real, VAR, box_diff<Real>()>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
             const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
             a.F[0][g] = Ff[0];
             a.F[1 + AX][g] = Ff[1];

@@ -34,6 +34,28 @@ enum CellQ {
     NCQ
 };
 
+// The FP64 sweep's cell box holds, after its difference pass, besides the
+// NCQ quantities of cell_fill_frame: the forward differences dF_c(i) =
+// F_c(i+1) - F_c(i) of the seven frame fluxes (planes C_DF0..C_DF6) and
+// du_c(i) = u_c(i+1) - u_c(i) of the conserved 7-vector -- in place of u_c
+// for rho, m and E (planes C_RHOQ, C_MN, C_MT1, C_MT2, C_E), in C_DU4, C_DU5
+// for B_t1, B_t2 (whose planes stay the primitives).
+enum BoxQ { C_DF0 = NCQ, C_DU4 = NCQ + 7, C_DU5, NBQ };
+
+// The difference pass pays in double, where the sweep is bound by the FP64
+// pipe and it removes 77 FP64 operations per interface (the stencil
+// differences and the central combination) for 14 per cell; in float its
+// extra barriers and shared-memory traffic cost more than the FP32
+// operations it saves.  Boxes of the compile-time tiles (sweep_tile_at):
+template <typename Real>
+__host__ __device__ constexpr bool box_diff() {
+    return sizeof(Real) == 8;
+}
+template <typename Real>
+__host__ __device__ constexpr int box_quantities() {
+    return box_diff<Real>() ? NBQ : NCQ;
+}
+
 template <typename Real>
 struct Phys {
     Real gamma, gm1, g1, g2;     // gamma, gamma-1, (gamma-1)/2, (gamma-2)/(gamma-1)
@@ -183,6 +205,36 @@ __device__ __forceinline__ void cell_fill_axis(Real *sm, int stride, Real rho, R
     const Real B1 = ax == 0 ? By : (ax == 1 ? Bz : Bx);
     const Real B2 = ax == 0 ? Bz : (ax == 1 ? Bx : By);
     cell_fill_frame<Real>(sm, stride, rho, mn, m1, m2, E, Bn, B1, B2, K, bad, hit);
+}
+
+// The difference pass of a sweep's cell box, in two steps around a barrier
+// (du overwrites u in place): box_diff_load reads the flux and conserved
+// 7-vectors of cell i and of its successor i + st along the sweep axis and
+// forms their differences; box_diff_store writes them.  sm points at the
+// box, `stride` elements between quantities.
+template <typename Real>
+struct CellDiff {
+    Real dF[7], dU[7];
+};
+
+template <typename Real>
+__device__ __forceinline__ void box_diff_load(const Real *sm, int stride, int i, int st, CellDiff<Real> &d) {
+    const Real *a = sm + i, *b = sm + i + st;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) d.dF[c] = b[(C_F0 + c) * stride] - a[(C_F0 + c) * stride];
+    constexpr int qU[7] = {C_RHOQ, C_MN, C_MT1, C_MT2, C_BT1, C_BT2, C_E};
+#pragma unroll
+    for (int c = 0; c < 7; ++c) d.dU[c] = b[qU[c] * stride] - a[qU[c] * stride];
+}
+
+template <typename Real>
+__device__ __forceinline__ void box_diff_store(Real *sm, int stride, int i, const CellDiff<Real> &d) {
+    Real *a = sm + i;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) a[(C_DF0 + c) * stride] = d.dF[c];
+    constexpr int qD[7] = {C_RHOQ, C_MN, C_MT1, C_MT2, C_DU4, C_DU5, C_E};
+#pragma unroll
+    for (int c = 0; c < 7; ++c) a[qD[c] * stride] = d.dU[c];
 }
 
 // fast signal speed |v_d| + c_f^d of a cell along axis d (Eq. cfl)
@@ -441,7 +493,7 @@ __device__ __forceinline__ void magnetosonic_pair(const Real (&X)[11][7], const 
 // six cells at sm + k*st (k = 0..5); quantities are `ncell` elements apart.
 // Ff receives the frame flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and
 // s1, s2 the CT transport fluxes F_{B_t} + <B_n v_t> of Eqs. (fct1)-(fct6).
-template <typename Real, int VAR>
+template <typename Real, int VAR, bool DIFF = false>
 __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell, int st, const Phys<Real> &K,
                                           Real (&Ff)[7], Real &s1, Real &s2) {
     using m = M<Real>;
@@ -450,21 +502,40 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     Real X[11][7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
-        const int qF = C_F0 + c;
-        const Real f0 = SMQ(qF, 0), f1 = SMQ(qF, 1), f2 = SMQ(qF, 2), f3 = SMQ(qF, 3), f4 = SMQ(qF, 4), f5 = SMQ(qF, 5);
-        X[0][c] = (Real(7) * (f2 + f3) - (f1 + f4)) * Real(1.0 / 12.0);
-        X[1][c] = f1 - f0;
-        X[2][c] = f2 - f1;
-        X[3][c] = f3 - f2;
-        X[4][c] = f4 - f3;
-        X[5][c] = f5 - f4;
-        const int qU = c == 0 ? C_RHOQ : c == 1 ? C_MN : c == 2 ? C_MT1 : c == 3 ? C_MT2 : c == 4 ? C_BT1 : c == 5 ? C_BT2 : C_E;
-        const Real u0 = SMQ(qU, 0), u1 = SMQ(qU, 1), u2 = SMQ(qU, 2), u3 = SMQ(qU, 3), u4 = SMQ(qU, 4), u5 = SMQ(qU, 5);
-        X[6][c] = u1 - u0;
-        X[7][c] = u2 - u1;
-        X[8][c] = u3 - u2;
-        X[9][c] = u4 - u3;
-        X[10][c] = u5 - u4;
+        if constexpr (DIFF) {
+            // from the box's forward differences (its difference pass):
+            // X[1 + j] = dF(j), X[6 + j] = du(j), j = 0..4, and the central
+            // combination (7 (f2 + f3) - (f1 + f4)) / 12 written as
+            // f2 + (6 dF(2) + dF(1) - dF(3)) / 12
+            const int qD = C_DF0 + c;
+            const int qU = c == 0 ? C_RHOQ : c == 1 ? C_MN : c == 2 ? C_MT1 : c == 3 ? C_MT2 : c == 4 ? C_DU4
+                           : c == 5 ? C_DU5 : C_E;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                X[1 + j][c] = SMQ(qD, j);
+                X[6 + j][c] = SMQ(qU, j);
+            }
+            X[0][c] = SMQ(C_F0 + c, 2) + (Real(6) * X[3][c] + X[2][c] - X[4][c]) * Real(1.0 / 12.0);
+        } else {
+            const int qF = C_F0 + c;
+            const Real f0 = SMQ(qF, 0), f1 = SMQ(qF, 1), f2 = SMQ(qF, 2), f3 = SMQ(qF, 3), f4 = SMQ(qF, 4),
+                       f5 = SMQ(qF, 5);
+            X[0][c] = (Real(7) * (f2 + f3) - (f1 + f4)) * Real(1.0 / 12.0);
+            X[1][c] = f1 - f0;
+            X[2][c] = f2 - f1;
+            X[3][c] = f3 - f2;
+            X[4][c] = f4 - f3;
+            X[5][c] = f5 - f4;
+            const int qU = c == 0 ? C_RHOQ : c == 1 ? C_MN : c == 2 ? C_MT1 : c == 3 ? C_MT2 : c == 4 ? C_BT1
+                           : c == 5 ? C_BT2 : C_E;
+            const Real u0 = SMQ(qU, 0), u1 = SMQ(qU, 1), u2 = SMQ(qU, 2), u3 = SMQ(qU, 3), u4 = SMQ(qU, 4),
+                       u5 = SMQ(qU, 5);
+            X[6][c] = u1 - u0;
+            X[7][c] = u2 - u1;
+            X[8][c] = u3 - u2;
+            X[9][c] = u4 - u3;
+            X[10][c] = u5 - u4;
+        }
     }
     // float: the central vector and the pairs (dF_j, du_j) for the packed
     // projection (the same values; only their grouping)
