@@ -326,13 +326,23 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
         W2 = 3.0 * (p2 * p2);
         Dn = W0 + 6.0 * (p1 * p1) + W2;
     } else {
-        // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2
+        // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2: with e_k =
+        // s_k^2 and E = e0 e1 e2, (e_k + tau^2) prod_{j != k} e_j = E + tau^2
+        // prod_{j != k} e_j, one FMA per weight; d = (1, 6, 3) enter the sum
+        // and the numerator by FMAs
         const double tau = fabs(I0 - I2);
         const double tt = tau * tau;
         const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
-        W0 = (e0 + tt) * (e1 * e2);
-        W2 = 3.0 * (e2 + tt) * (e0 * e1);
-        Dn = W0 + 6.0 * (e1 + tt) * (e0 * e2) + W2;
+        const double e12 = e1 * e2, e02 = e0 * e2, e01 = e0 * e1;
+        const double E = e0 * e12;
+        W0 = fma(tt, e12, E);
+        const double V1 = fma(tt, e02, E), V2 = fma(tt, e01, E);
+        Dn = fma(3.0, V2, fma(6.0, V1, W0));
+        // phi_numerator with a_2 = 3 V2: (a - 2b + c) W0 + (3 V2 - D/2)((b + d)/2 - c)
+        const double t1 = (a - 2.0 * b) + c;
+        const double t2h = 0.5 * (b + d) - c;
+        Nn = W0 * t1 + fma(3.0, V2, -0.5 * Dn) * t2h;
+        return;
     }
     Nn = phi_numerator<double>(a, b, c, d, W0, W2, Dn);
 }
