@@ -432,56 +432,14 @@ __device__ __forceinline__ void split_pair_f(float Pc0, const float2 (&Pc2)[5], 
     unpack11(Pc0 - Ps0, D, Pl);
 }
 
-// magnetosonic_pair (below) with the float packed projection
-template <int VAR>
-__device__ __forceinline__ void magnetosonic_pair_f(const float (&X0)[7], const float2 (&X2)[5][7],
-                                                    const float (&Lc)[7], const float (&Ls)[4], const float (&Rc)[7],
-                                                    const float (&Rs)[4], float alu, float all, float eps,
-                                                    float (&Ff)[7], bool first) {
-    constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
-    constexpr int cs[4] = {0, 1, 2, 3};
-    float pc0, ps0;
-    float2 pc2[5], ps2[5];
-    project_f<7>(X0, X2, cc, Lc, pc0, pc2);
-    project_f<4>(X0, X2, cs, Ls, ps0, ps2);
-    float Pu[11], Pl[11];
-    split_pair_f(pc0, pc2, ps0, ps2, Pu, Pl);
-    const float Fu = weno_field<float, VAR>(Pu, alu, eps);
-    const float Fl = weno_field<float, VAR>(Pl, all, eps);
-    const float sum = Fu + Fl, dif = Fu - Fl;
-    if (first) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) Ff[c] = sum * Rc[c];
-    } else {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) Ff[c] += sum * Rc[c];
-    }
-    Ff[1] += dif * Rs[0];
-    Ff[2] += dif * Rs[1];
-    Ff[3] += dif * Rs[2];
-    Ff[6] += dif * Rs[3];
-}
-
-// One magnetosonic (fast or slow) pair of characteristic fields: the left
-// eigenvectors are Lc + Ls and Lc - Ls (Ls non-zero in rows 0..3), the right
-// ones Rc + Rs and Rc - Rs (Rs non-zero in rows 1, 2, 3, 6).  The first
-// call initialises the frame flux Ff.
+// The WENO fluxes of a mode pair from its two projected stencils (Pu for the
+// left eigenvector Lc + Ls, Pl for Lc - Ls) and their back-projection with
+// the right eigenvectors Rc +- Rs (Rs non-zero in rows 1, 2, 3, 6) into the
+// frame flux Ff; the first call initialises Ff.
 template <typename Real, int VAR>
-__device__ __forceinline__ void magnetosonic_pair(const Real (&X)[11][7], const Real (&Lc)[7], const Real (&Ls)[4],
-                                                  const Real (&Rc)[7], const Real (&Rs)[4], Real alu, Real all,
-                                                  Real eps, Real (&Ff)[7], bool first) {
-    Real Pu[11], Pl[11];
-#pragma unroll
-    for (int x = 0; x < 11; ++x) {
-        Real pc = Lc[0] * X[x][0];
-#pragma unroll
-        for (int c = 1; c < 7; ++c) pc += Lc[c] * X[x][c];
-        Real ps = Ls[0] * X[x][0];
-#pragma unroll
-        for (int c = 1; c < 4; ++c) ps += Ls[c] * X[x][c];
-        Pu[x] = pc + ps;
-        Pl[x] = pc - ps;
-    }
+__device__ __forceinline__ void pair_finish(const Real (&Pu)[11], const Real (&Pl)[11], const Real (&Rc)[7],
+                                            const Real (&Rs)[4], Real alu, Real all, Real eps, Real (&Ff)[7],
+                                            bool first) {
     const Real Fu = weno_field<Real, VAR>(Pu, alu, eps);
     const Real Fl = weno_field<Real, VAR>(Pl, all, eps);
     const Real sum = Fu + Fl, dif = Fu - Fl;
@@ -631,36 +589,79 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     const Real Gs = as * csl * vn + af * cf * sg * bv;
     const Real ics2 = m::rcp_(cs2);
     const Real pre = Real(0.5) * ics2;
-    const Real tau = K.gm1 * ics2;
     const Real eps = Real(4.0 / 3.0) * K.eps_w;   // 4 eps / 3: see weno_field
+
+    // The sign-free parts of the fast and slow left eigenvectors and the
+    // entropy left eigenvector are combinations of two common vectors,
+    //   G = (g1 v^2, -gm1 v_n, -gm1 v_t1, -gm1 v_t2, -gm1 B_t1, -gm1 B_t2, gm1),
+    //   H = (0, 0, 0, 0, b_1, b_2, 0):
+    //   Lc_fast = pre (a_f G + sqrt(rho) c_s a_s H),
+    //   Lc_slow = pre (a_s G - sqrt(rho) c_s a_f H),
+    //   L_entropy = e_0 - G / c_s^2   (e_0 the unit vector of the density),
+    // so each stencil vector is projected on G and H once.
+    const Real G[7] = {K.g1 * v2, -K.gm1 * vn, -K.gm1 * vt1, -K.gm1 * vt2, -K.gm1 * Bt1, -K.gm1 * Bt2, Real(K.gm1)};
+    [[maybe_unused]] Real gX[11], hX[11];     // double: G.X, H.X
+    [[maybe_unused]] float g0, h0;            // float: the central vector's and
+    [[maybe_unused]] float2 g2[5], h2[5];     // the five pairs' projections
+    if constexpr (std::is_same<Real, float>::value) {
+        constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
+        constexpr int ch[2] = {4, 5};
+        const float Hc[2] = {b1, b2};
+        project_f<7>(X0f, X2f, cc, G, g0, g2);
+        project_f<2>(X0f, X2f, ch, Hc, h0, h2);
+    } else {
+#pragma unroll
+        for (int x = 0; x < 11; ++x) {
+            Real gx = G[0] * X[x][0];
+#pragma unroll
+            for (int c = 1; c < 7; ++c) gx += G[c] * X[x][c];
+            gX[x] = gx;
+            hX[x] = b1 * X[x][4] + b2 * X[x][5];
+        }
+    }
+    // one magnetosonic pair: Lc = cg G + ch H, Ls (rows 0..3) on the stencil
+    auto magnetosonic = [&](Real cg, Real ch, const Real (&Ls)[4], const Real (&Rc)[7], const Real (&Rs)[4], Real alu,
+                            Real all, bool first) {
+        Real Pu[11], Pl[11];
+        if constexpr (std::is_same<Real, float>::value) {
+            constexpr int cs4[4] = {0, 1, 2, 3};
+            const float pc0 = cg * g0 + ch * h0;
+            float2 pc2[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) pc2[j] = __ffma2_rn(bcast2(cg), g2[j], __fmul2_rn(bcast2(ch), h2[j]));
+            float ps0;
+            float2 ps2[5];
+            project_f<4>(X0f, X2f, cs4, Ls, ps0, ps2);
+            split_pair_f(pc0, pc2, ps0, ps2, Pu, Pl);
+        } else {
+#pragma unroll
+            for (int x = 0; x < 11; ++x) {
+                const Real pc = cg * gX[x] + ch * hX[x];
+                Real ps = Ls[0] * X[x][0];
+#pragma unroll
+                for (int c = 1; c < 4; ++c) ps += Ls[c] * X[x][c];
+                Pu[x] = pc + ps;
+                Pl[x] = pc - ps;
+            }
+        }
+        pair_finish<Real, VAR>(Pu, Pl, Rc, Rs, alu, all, eps, Ff, first);
+    };
 
     // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
     {
-        const Real k1 = -K.gm1 * af;
-        const Real Lc[7] = {pre * K.g1 * af * v2, pre * k1 * vn, pre * k1 * vt1, pre * k1 * vt2,
-                            pre * (k1 * Bt1 + sr * cs * as * b1), pre * (k1 * Bt2 + sr * cs * as * b2), pre * K.gm1 * af};
         const Real Ls[4] = {pre * Gf, -pre * af * cf, pre * csl * as * b1 * sg, pre * csl * as * b2 * sg};
         const Real Rc[7] = {af, af * vn, af * vt1, af * vt2, cs * as * b1 * isr, cs * as * b2 * isr,
                             af * (Real(0.5) * v2 + cf2 - K.g2 * cs2)};
         const Real Rs[4] = {-af * cf, csl * as * b1 * sg, csl * as * b2 * sg, -Gf};   // rows 1, 2, 3, 6
-        if constexpr (std::is_same<Real, float>::value)
-            magnetosonic_pair_f<VAR>(X0f, X2f, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
-        else
-            magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_fm, al_fp, eps, Ff, true);
+        magnetosonic(pre * af, pre * (sr * cs * as), Ls, Rc, Rs, al_fm, al_fp, true);
     }
     // ---- slow pair: m = 3 (v - c_slow, upper sign) and m = 5 (v + c_slow)
     {
-        const Real k2 = -K.gm1 * as;
-        const Real Lc[7] = {pre * K.g1 * as * v2, pre * k2 * vn, pre * k2 * vt1, pre * k2 * vt2,
-                            pre * (k2 * Bt1 - sr * cs * af * b1), pre * (k2 * Bt2 - sr * cs * af * b2), pre * K.gm1 * as};
         const Real Ls[4] = {pre * Gs, -pre * as * csl, -pre * cf * af * b1 * sg, -pre * cf * af * b2 * sg};
         const Real Rc[7] = {as, as * vn, as * vt1, as * vt2, -cs * af * b1 * isr, -cs * af * b2 * isr,
                             as * (Real(0.5) * v2 + csl2 - K.g2 * cs2)};
         const Real Rs[4] = {-as * csl, -cf * af * b1 * sg, -cf * af * b2 * sg, -Gs};
-        if constexpr (std::is_same<Real, float>::value)
-            magnetosonic_pair_f<VAR>(X0f, X2f, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
-        else
-            magnetosonic_pair<Real, VAR>(X, Lc, Ls, Rc, Rs, al_sm, al_sp, eps, Ff, false);
+        magnetosonic(pre * as, -(pre * (sr * cs * af)), Ls, Rc, Rs, al_sm, al_sp, false);
     }
     // ---- Alfven pair: m = 2 (v - c_A, upper sign) and m = 6 (v + c_A)
     {
@@ -696,24 +697,17 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         Ff[4] += dif * (-b2 * isr);
         Ff[5] += dif * (b1 * isr);
     }
-    // ---- entropy field: m = 4 (v)
+    // ---- entropy field: m = 4 (v), L = e_0 - G / c_s^2
     {
-        const Real L[7] = {Real(1) - Real(0.5) * tau * v2, tau * vn, tau * vt1, tau * vt2, tau * Bt1, tau * Bt2, -tau};
         Real Pe[11];
         if constexpr (std::is_same<Real, float>::value) {
-            constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
-            float pe0;
             float2 pe2[5];
-            project_f<7>(X0f, X2f, cc, L, pe0, pe2);
-            unpack11(pe0, pe2, Pe);
+#pragma unroll
+            for (int j = 0; j < 5; ++j) pe2[j] = __ffma2_rn(bcast2(-ics2), g2[j], X2f[j][0]);
+            unpack11(__fmaf_rn(-ics2, g0, X0f[0]), pe2, Pe);
         } else {
 #pragma unroll
-            for (int x = 0; x < 11; ++x) {
-                Real pc = L[0] * X[x][0];
-#pragma unroll
-                for (int c = 1; c < 7; ++c) pc += L[c] * X[x][c];
-                Pe[x] = pc;
-            }
+            for (int x = 0; x < 11; ++x) Pe[x] = X[x][0] - ics2 * gX[x];
         }
         const Real Fe = weno_field<Real, VAR>(Pe, al_e, eps);
         Ff[0] += Fe;
