@@ -432,30 +432,6 @@ __device__ __forceinline__ void split_pair_f(float Pc0, const float2 (&Pc2)[5], 
     unpack11(Pc0 - Ps0, D, Pl);
 }
 
-// The WENO fluxes of a mode pair from its two projected stencils (Pu for the
-// left eigenvector Lc + Ls, Pl for Lc - Ls) and their back-projection with
-// the right eigenvectors Rc +- Rs (Rs non-zero in rows 1, 2, 3, 6) into the
-// frame flux Ff; the first call initialises Ff.
-template <typename Real, int VAR>
-__device__ __forceinline__ void pair_finish(const Real (&Pu)[11], const Real (&Pl)[11], const Real (&Rc)[7],
-                                            const Real (&Rs)[4], Real alu, Real all, Real eps, Real (&Ff)[7],
-                                            bool first) {
-    const Real Fu = weno_field<Real, VAR>(Pu, alu, eps);
-    const Real Fl = weno_field<Real, VAR>(Pl, all, eps);
-    const Real sum = Fu + Fl, dif = Fu - Fl;
-    if (first) {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) Ff[c] = sum * Rc[c];
-    } else {
-#pragma unroll
-        for (int c = 0; c < 7; ++c) Ff[c] += sum * Rc[c];
-    }
-    Ff[1] += dif * Rs[0];
-    Ff[2] += dif * Rs[1];
-    Ff[3] += dif * Rs[2];
-    Ff[6] += dif * Rs[3];
-}
-
 // ---------------------------------------------------------------- one face
 // Characteristic WENO flux at the face between stencil cells 2 and 3 of the
 // six cells at sm + k*st (k = 0..5); quantities are `ncell` elements apart.
@@ -593,13 +569,14 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
 
     // The sign-free parts of the fast and slow left eigenvectors and the
     // entropy left eigenvector are combinations of two common vectors,
-    //   G = (g1 v^2, -gm1 v_n, -gm1 v_t1, -gm1 v_t2, -gm1 B_t1, -gm1 B_t2, gm1),
+    //   G = (v^2 / 2, -v_n, -v_t1, -v_t2, -B_t1, -B_t2, 1),
     //   H = (0, 0, 0, 0, b_1, b_2, 0):
-    //   Lc_fast = pre (a_f G + sqrt(rho) c_s a_s H),
-    //   Lc_slow = pre (a_s G - sqrt(rho) c_s a_f H),
-    //   L_entropy = e_0 - G / c_s^2   (e_0 the unit vector of the density),
-    // so each stencil vector is projected on G and H once.
-    const Real G[7] = {K.g1 * v2, -K.gm1 * vn, -K.gm1 * vt1, -K.gm1 * vt2, -K.gm1 * Bt1, -K.gm1 * Bt2, Real(K.gm1)};
+    //   Lc_fast = pre ((gamma - 1) a_f G + sqrt(rho) c_s a_s H),
+    //   Lc_slow = pre ((gamma - 1) a_s G - sqrt(rho) c_s a_f H),
+    //   L_entropy = e_0 - (gamma - 1) G / c_s^2   (e_0: the density's unit vector),
+    // so each stencil vector is projected on G (its last component, 1, needs
+    // no product) and H once.
+    const Real G[7] = {Real(0.5) * v2, -vn, -vt1, -vt2, -Bt1, -Bt2, Real(1)};
     [[maybe_unused]] Real gX[11], hX[11];     // double: G.X, H.X
     [[maybe_unused]] float g0, h0;            // float: the central vector's and
     [[maybe_unused]] float2 g2[5], h2[5];     // the five pairs' projections
@@ -607,21 +584,21 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         constexpr int cc[7] = {0, 1, 2, 3, 4, 5, 6};
         constexpr int ch[2] = {4, 5};
         const float Hc[2] = {b1, b2};
-        project_f<7>(X0f, X2f, cc, G, g0, g2);
+        project_f<7>(X0f, X2f, cc, G, g0, g2);   // (the compiler drops the factor 1)
         project_f<2>(X0f, X2f, ch, Hc, h0, h2);
     } else {
 #pragma unroll
         for (int x = 0; x < 11; ++x) {
-            Real gx = G[0] * X[x][0];
+            Real gx = X[x][6] + G[0] * X[x][0];
 #pragma unroll
-            for (int c = 1; c < 7; ++c) gx += G[c] * X[x][c];
+            for (int c = 1; c < 6; ++c) gx += G[c] * X[x][c];
             gX[x] = gx;
             hX[x] = b1 * X[x][4] + b2 * X[x][5];
         }
     }
-    // one magnetosonic pair: Lc = cg G + ch H, Ls (rows 0..3) on the stencil
-    auto magnetosonic = [&](Real cg, Real ch, const Real (&Ls)[4], const Real (&Rc)[7], const Real (&Rs)[4], Real alu,
-                            Real all, bool first) {
+    // The WENO fluxes (Fu for the left eigenvector Lc + Ls, Fl for Lc - Ls)
+    // of one magnetosonic pair: Lc = cg G + ch H, Ls non-zero in rows 0..3.
+    auto magnetosonic = [&](Real cg, Real ch, const Real (&Ls)[4], Real alu, Real all, Real &Fu, Real &Fl) {
         Real Pu[11], Pl[11];
         if constexpr (std::is_same<Real, float>::value) {
             constexpr int cs4[4] = {0, 1, 2, 3};
@@ -644,29 +621,33 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
                 Pl[x] = pc - ps;
             }
         }
-        pair_finish<Real, VAR>(Pu, Pl, Rc, Rs, alu, all, eps, Ff, first);
+        Fu = weno_field<Real, VAR>(Pu, alu, eps);
+        Fl = weno_field<Real, VAR>(Pl, all, eps);
     };
 
     // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
+    Real sf, df;
     {
         const Real Ls[4] = {pre * Gf, -pre * af * cf, pre * csl * as * b1 * sg, pre * csl * as * b2 * sg};
-        const Real Rc[7] = {af, af * vn, af * vt1, af * vt2, cs * as * b1 * isr, cs * as * b2 * isr,
-                            af * (Real(0.5) * v2 + cf2 - K.g2 * cs2)};
-        const Real Rs[4] = {-af * cf, csl * as * b1 * sg, csl * as * b2 * sg, -Gf};   // rows 1, 2, 3, 6
-        magnetosonic(pre * af, pre * (sr * cs * as), Ls, Rc, Rs, al_fm, al_fp, true);
+        Real Fu, Fl;
+        magnetosonic(pre * (K.gm1 * af), pre * (sr * cs * as), Ls, al_fm, al_fp, Fu, Fl);
+        sf = Fu + Fl;
+        df = Fu - Fl;
     }
     // ---- slow pair: m = 3 (v - c_slow, upper sign) and m = 5 (v + c_slow)
+    Real ss, ds;
     {
         const Real Ls[4] = {pre * Gs, -pre * as * csl, -pre * cf * af * b1 * sg, -pre * cf * af * b2 * sg};
-        const Real Rc[7] = {as, as * vn, as * vt1, as * vt2, -cs * af * b1 * isr, -cs * af * b2 * isr,
-                            as * (Real(0.5) * v2 + csl2 - K.g2 * cs2)};
-        const Real Rs[4] = {-as * csl, -cf * af * b1 * sg, -cf * af * b2 * sg, -Gs};
-        magnetosonic(pre * as, -(pre * (sr * cs * af)), Ls, Rc, Rs, al_sm, al_sp, false);
+        Real Fu, Fl;
+        magnetosonic(pre * (K.gm1 * as), -(pre * (sr * cs * af)), Ls, al_sm, al_sp, Fu, Fl);
+        ss = Fu + Fl;
+        ds = Fu - Fl;
     }
     // ---- Alfven pair: m = 2 (v - c_A, upper sign) and m = 6 (v + c_A)
+    //   L = (Ga/2, 0, -b2 sg/2, b1 sg/2, -+ sr b2/2, +- sr b1/2, 0)
+    //   R = (0, 0, -b2 sg, b1 sg, -+ b2/sr, +- b1/sr, -Ga)
+    Real sa, da;
     {
-        // L = (Ga/2, 0, -b2 sg/2, b1 sg/2, -+ sr b2/2, +- sr b1/2, 0)
-        // R = (0, 0, -b2 sg, b1 sg, -+ b2/sr, +- b1/sr, -Ga)
         const Real l0 = Real(0.5) * Ga, l2 = Real(-0.5) * b2 * sg, l3 = Real(0.5) * b1 * sg;
         const Real l4 = Real(-0.5) * sr * b2, l5 = Real(0.5) * sr * b1;
         Real Pu[11], Pl[11];
@@ -690,31 +671,47 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         }
         const Real Fu = weno_field<Real, VAR>(Pu, al_am, eps);
         const Real Fl = weno_field<Real, VAR>(Pl, al_ap, eps);
-        const Real sum = Fu + Fl, dif = Fu - Fl;
-        Ff[2] += sum * (-b2 * sg);
-        Ff[3] += sum * (b1 * sg);
-        Ff[6] += sum * (-Ga);
-        Ff[4] += dif * (-b2 * isr);
-        Ff[5] += dif * (b1 * isr);
+        sa = Fu + Fl;
+        da = Fu - Fl;
     }
-    // ---- entropy field: m = 4 (v), L = e_0 - G / c_s^2
+    // ---- entropy field: m = 4 (v), L = e_0 - (gamma - 1) G / c_s^2
+    Real Fe;
     {
+        const Real tau = K.gm1 * ics2;
         Real Pe[11];
         if constexpr (std::is_same<Real, float>::value) {
             float2 pe2[5];
 #pragma unroll
-            for (int j = 0; j < 5; ++j) pe2[j] = __ffma2_rn(bcast2(-ics2), g2[j], X2f[j][0]);
-            unpack11(__fmaf_rn(-ics2, g0, X0f[0]), pe2, Pe);
+            for (int j = 0; j < 5; ++j) pe2[j] = __ffma2_rn(bcast2(-tau), g2[j], X2f[j][0]);
+            unpack11(__fmaf_rn(-tau, g0, X0f[0]), pe2, Pe);
         } else {
 #pragma unroll
-            for (int x = 0; x < 11; ++x) Pe[x] = X[x][0] - ics2 * gX[x];
+            for (int x = 0; x < 11; ++x) Pe[x] = X[x][0] - tau * gX[x];
         }
-        const Real Fe = weno_field<Real, VAR>(Pe, al_e, eps);
-        Ff[0] += Fe;
-        Ff[1] += Fe * vn;
-        Ff[2] += Fe * vt1;
-        Ff[3] += Fe * vt2;
-        Ff[6] += Fe * (Real(0.5) * v2);
+        Fe = weno_field<Real, VAR>(Pe, al_e, eps);
+    }
+    // ---- back-projection: F = sum over fields of (WENO flux) x (right
+    // eigenvector).  The right eigenvectors of the fast pair (Rc +- Rs),
+    //   Rc = (a_f, a_f v, c_s a_s b / sqrt(rho), a_f (v^2/2 + c_f^2 - g2 c_s^2)),
+    //   Rs = rows (1, 2, 3, 6): (-a_f c_f, c_slow a_s b sg, -Gf),
+    // of the slow pair (a_f, c_f -> a_s, c_slow and a_s, c_slow -> -a_f, c_f
+    // in Rc's field rows and Rs) and of the entropy field (1, v, 0, v^2 / 2)
+    // share R1 = (1, v, 0, 0, v^2/2 - g2 c_s^2) and (0, 0, 0, 0, b_1, b_2, 0),
+    // so the sums (Fu + Fl) and differences (Fu - Fl) of the fields combine
+    // into a few scalars first.
+    {
+        const Real S1 = af * sf + as * ss + Fe;
+        const Real S2 = (cs * isr) * (as * sf - af * ss);
+        const Real T1 = -(af * cf * df + as * csl * ds);
+        const Real T2 = sg * (csl * as * df - cf * af * ds);
+        const Real w = Real(0.5) * v2 - K.g2 * cs2;
+        Ff[0] = S1;
+        Ff[1] = S1 * vn + T1;
+        Ff[2] = S1 * vt1 + T2 * b1 - sa * (b2 * sg);
+        Ff[3] = S1 * vt2 + T2 * b2 + sa * (b1 * sg);
+        Ff[4] = S2 * b1 - da * (b2 * isr);
+        Ff[5] = S2 * b2 + da * (b1 * isr);
+        Ff[6] = S1 * w + af * cf2 * sf + as * csl2 * ss + K.g2 * cs2 * Fe - (Gf * df + Gs * ds) - sa * Ga;
     }
     s1 = Ff[4] + bvt1;
     s2 = Ff[5] + bvt2;
