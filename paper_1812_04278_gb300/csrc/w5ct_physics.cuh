@@ -259,29 +259,27 @@ __device__ __forceinline__ Real signal_speed(Real r, Real vn, Real P, Real Bn, R
 //   d_k / (eps + IS_k)^2 normalised; WENO-Z: tau_5 / (eps + IS_k)), so the
 //   smoothness indicators are evaluated as IS_k / 3 = (13/3) x^2 + y^2 with
 //   eps / 3 (the caller passes it);
-// * with w_k = a_k / D (D = a_0 + a_1 + a_2),
-//   phi_N = w_0 (a - 2b + c)/3 + (w_2 - 1/2)(b - 2c + d)/6
-//         = [a_0 (a - 2b + c) + (a_2 - D/2)((b + d)/2 - c)] / (3 D);
+// * with w_k = a_k / D (D = a_0 + a_1 + a_2) and the second differences
+//   t1 = a - 2b + c = x0 - y0, t2 = b - 2c + d = y0 - z0 of the first ones
+//   (x0 = a - b, y0 = b - c, z0 = c - d, also those of the indicators),
+//   phi_N = w_0 t1 / 3 + (w_2 - 1/2) t2 / 6
+//         = [a_0 t1 + (a_2 / 2 - D / 4) t2] / (3 D);
 //   in double each interpolant returns that numerator and D, and weno_field
 //   divides once for the two; in float the weights are normalised first
 //   (D = 1) and phi_N = Nn / 3.
 template <typename Real>
-__device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real &I0, Real &I1, Real &I2) {
+__device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real &I0, Real &I1, Real &I2, Real &x0,
+                                            Real &y0, Real &z0) {
     const Real k = Real(13.0 / 3.0);
-    const Real x0 = a - b, x1 = a - Real(3) * b;
+    x0 = a - b;
+    const Real x1 = a - Real(3) * b;
     I0 = (k * x0) * x0 + x1 * x1;
-    const Real y0 = b - c, y1 = b + c;
+    y0 = b - c;
+    const Real y1 = b + c;
     I1 = (k * y0) * y0 + y1 * y1;
-    const Real z0 = c - d, z1 = Real(3) * c - d;
+    z0 = c - d;
+    const Real z1 = Real(3) * c - d;
     I2 = (k * z0) * z0 + z1 * z1;
-}
-
-// numerator [a_0 (a - 2b + c) + (a_2 - D/2)((b + d)/2 - c)] of phi_N
-template <typename Real>
-__device__ __forceinline__ Real phi_numerator(Real a, Real b, Real c, Real d, Real a0, Real a2, Real D) {
-    const Real t1 = (a - Real(2) * b) + c;
-    const Real t2h = Real(0.5) * (b + d) - c;
-    return a0 * t1 + (a2 - Real(0.5) * D) * t2h;
 }
 
 // float: phi_N = Nn / 3 with the weights normalised here by one reciprocal
@@ -289,8 +287,8 @@ __device__ __forceinline__ Real phi_numerator(Real a, Real b, Real c, Real d, Re
 // overflows; unnormalised WENO-Z weights reach 1e36 in float)
 template <int VAR>
 __device__ __forceinline__ float phi_nf(float a, float b, float c, float d, float eps3) {
-    float I0, I1, I2;
-    smoothness3<float>(a, b, c, d, I0, I1, I2);
+    float I0, I1, I2, x0, y0, z0;
+    smoothness3<float>(a, b, c, d, I0, I1, I2, x0, y0, z0);
     const float s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
     float a0, a1, a2;
     if constexpr (VAR == 0) {
@@ -307,44 +305,41 @@ __device__ __forceinline__ float phi_nf(float a, float b, float c, float d, floa
         a2 = 3.0f * (1.0f + r2 * r2);
     }
     const float inv = __fdividef(1.0f, (a0 + a1) + a2);
-    return phi_numerator<float>(a, b, c, d, a0 * inv, a2 * inv, 1.0f);
+    return (a0 * inv) * (x0 - y0) + __fmaf_rn(a2, 0.5f * inv, -0.25f) * (y0 - z0);
 }
 
 // double: the weights times the common factor (s_0 s_1 s_2)^2, so that no
 // weight needs a division; phi_N = Nn / (3 D), and the two interpolants of
-// one field share a single division in weno_field.
+// one field share a single division in weno_field.  The linear weights
+// d = (1, 6, 3) enter the sum and the numerator by FMAs.
 template <int VAR>
 __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, double eps3, double &Nn, double &Dn) {
-    double I0, I1, I2;
-    smoothness3<double>(a, b, c, d, I0, I1, I2);
+    double I0, I1, I2, x0, y0, z0;
+    smoothness3<double>(a, b, c, d, I0, I1, I2, x0, y0, z0);
     const double s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
-    double W0, W2;
+    double W0, V1, V2;   // alpha_k / d_k times the common factor
     if constexpr (VAR == 0) {
         // alpha_k = d_k / s_k^2 times (s0 s1 s2)^2
         const double p0 = s1 * s2, p1 = s0 * s2, p2 = s0 * s1;
         W0 = p0 * p0;
-        W2 = 3.0 * (p2 * p2);
-        Dn = W0 + 6.0 * (p1 * p1) + W2;
+        V1 = p1 * p1;
+        V2 = p2 * p2;
     } else {
         // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2: with e_k =
         // s_k^2 and E = e0 e1 e2, (e_k + tau^2) prod_{j != k} e_j = E + tau^2
-        // prod_{j != k} e_j, one FMA per weight; d = (1, 6, 3) enter the sum
-        // and the numerator by FMAs
+        // prod_{j != k} e_j, one FMA per weight
         const double tau = fabs(I0 - I2);
         const double tt = tau * tau;
         const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
         const double e12 = e1 * e2, e02 = e0 * e2, e01 = e0 * e1;
         const double E = e0 * e12;
         W0 = fma(tt, e12, E);
-        const double V1 = fma(tt, e02, E), V2 = fma(tt, e01, E);
-        Dn = fma(3.0, V2, fma(6.0, V1, W0));
-        // phi_numerator with a_2 = 3 V2: (a - 2b + c) W0 + (3 V2 - D/2)((b + d)/2 - c)
-        const double t1 = (a - 2.0 * b) + c;
-        const double t2h = 0.5 * (b + d) - c;
-        Nn = W0 * t1 + fma(3.0, V2, -0.5 * Dn) * t2h;
-        return;
+        V1 = fma(tt, e02, E);
+        V2 = fma(tt, e01, E);
     }
-    Nn = phi_numerator<double>(a, b, c, d, W0, W2, Dn);
+    Dn = fma(3.0, V2, fma(6.0, V1, W0));
+    // a_0 t1 + (a_2 / 2 - D / 4) t2 with a_2 = 3 V2
+    Nn = W0 * (x0 - y0) + fma(1.5, V2, -0.25 * Dn) * (y0 - z0);
 }
 
 // Eq. (FWENO) for one characteristic field from its 11 projections:
