@@ -114,9 +114,9 @@ template <> struct M<float> {
 };
 
 // ---------------------------------------------------------------- wave speeds
-// c_f^2 - c_s^2 (fmc) and c_s^2 - c_slow^2 (cms) without cancellation.
+// c_f^2 - c_s^2 (fmc), c_s^2 - c_slow^2 (cms) without cancellation, and c_f^2.
 template <typename Real>
-__device__ __forceinline__ void speeds(Real cs2, Real ca2, Real bt2, Real &fmc, Real &cms, Real &cf2, Real &csl2) {
+__device__ __forceinline__ void speeds_fast(Real cs2, Real ca2, Real bt2, Real &fmc, Real &cms, Real &cf2) {
     using m = M<Real>;
     const Real dd = (cs2 - ca2) * (cs2 - ca2) + bt2 * (bt2 + Real(2) * ca2 + Real(2) * cs2);
     const Real sd = m::sqrt_(dd);
@@ -129,7 +129,13 @@ __device__ __forceinline__ void speeds(Real cs2, Real ca2, Real bt2, Real &fmc, 
         fmc = cms > Real(0) ? m::div_(cs2 * bt2, cms) : Real(0);
     }
     cf2 = cs2 + fmc;
-    csl2 = cf2 > Real(0) ? m::div_(cs2 * ca2, cf2) : Real(0);
+}
+
+// speeds_fast and c_slow^2 = c_s^2 c_A^2 / c_f^2.
+template <typename Real>
+__device__ __forceinline__ void speeds(Real cs2, Real ca2, Real bt2, Real &fmc, Real &cms, Real &cf2, Real &csl2) {
+    speeds_fast<Real>(cs2, ca2, bt2, fmc, cms, cf2);
+    csl2 = cf2 > Real(0) ? M<Real>::div_(cs2 * ca2, cf2) : Real(0);
 }
 
 // ---------------------------------------------------------------- one cell
@@ -530,8 +536,13 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
     Real cs2 = K.gamma * P * ir;
     if constexpr (float_based<Real>) cs2 = m::max_(cs2, K.cs2_rel * (v2 + ca2 + bt2));
     Real fmc, cms, cf2, csl2;
-    speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
-    const Real cf = m::sqrt_(cf2), csl = m::sqrt_(csl2), cs = m::sqrt_(cs2);
+    speeds_fast<Real>(cs2, ca2, bt2, fmc, cms, cf2);
+    const Real sr = m::sqrt_(r);
+    const Real isr = sr * ir;
+    // c_slow = c_s c_A / c_f (c_slow^2 = c_s^2 c_A^2 / c_f^2), c_A = |B_n| / sqrt(rho)
+    const Real cf = m::sqrt_(cf2), cs = m::sqrt_(cs2);
+    const Real csl = cf > Real(0) ? cs * (m::abs_(Bn) * isr) * m::rcp_(cf) : Real(0);
+    csl2 = csl * csl;
     const Real dfs = fmc + cms;   // c_f^2 - c_slow^2
     Real af, as;
     if (dfs >= K.eps_b2) {
@@ -552,8 +563,6 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
         b2 = Real(0.70710678118654752440);
     }
     const Real sg = (Bn >= K.eps_b) ? Real(1) : Real(-1);
-    const Real sr = m::sqrt_(r);
-    const Real isr = sr * ir;
     const Real bv = b1 * vt1 + b2 * vt2;
     const Real Gf = af * cf * vn - as * csl * sg * bv;
     const Real Ga = sg * (b2 * vt1 - b1 * vt2);
