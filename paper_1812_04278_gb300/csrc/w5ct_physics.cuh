@@ -273,19 +273,22 @@ __device__ __forceinline__ Real signal_speed(Real r, Real vn, Real P, Real Bn, R
 //   in double each interpolant returns that numerator and D, and weno_field
 //   divides once for the two; in float the weights are normalised first
 //   (D = 1) and phi_N = Nn / 3.
+//
+// smoothness3 returns s_k = eps/3 + IS_k/3, the epsilon added inside the
+// last FMA of each indicator, and the first differences x0, y0, z0.
 template <typename Real>
-__device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real &I0, Real &I1, Real &I2, Real &x0,
-                                            Real &y0, Real &z0) {
+__device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real eps3, Real &s0, Real &s1, Real &s2,
+                                            Real &x0, Real &y0, Real &z0) {
     const Real k = Real(13.0 / 3.0);
     x0 = a - b;
     const Real x1 = a - Real(3) * b;
-    I0 = (k * x0) * x0 + x1 * x1;
+    s0 = (k * x0) * x0 + (x1 * x1 + eps3);
     y0 = b - c;
     const Real y1 = b + c;
-    I1 = (k * y0) * y0 + y1 * y1;
+    s1 = (k * y0) * y0 + (y1 * y1 + eps3);
     z0 = c - d;
     const Real z1 = Real(3) * c - d;
-    I2 = (k * z0) * z0 + z1 * z1;
+    s2 = (k * z0) * z0 + (z1 * z1 + eps3);
 }
 
 // float: phi_N = Nn / 3 with the weights normalised here by one reciprocal
@@ -293,16 +296,15 @@ __device__ __forceinline__ void smoothness3(Real a, Real b, Real c, Real d, Real
 // overflows; unnormalised WENO-Z weights reach 1e36 in float)
 template <int VAR>
 __device__ __forceinline__ float phi_nf(float a, float b, float c, float d, float eps3) {
-    float I0, I1, I2, x0, y0, z0;
-    smoothness3<float>(a, b, c, d, I0, I1, I2, x0, y0, z0);
-    const float s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
+    float s0, s1, s2, x0, y0, z0;
+    smoothness3<float>(a, b, c, d, eps3, s0, s1, s2, x0, y0, z0);
     float a0, a1, a2;
     if constexpr (VAR == 0) {
         a0 = __fdividef(1.0f, s0 * s0);
         a1 = 6.0f * __fdividef(1.0f, s1 * s1);
         a2 = 3.0f * __fdividef(1.0f, s2 * s2);
     } else {
-        const float tau = fabsf(I0 - I2);
+        const float tau = fabsf(s0 - s2);   // |IS_0 - IS_2| / 3
         const float r0 = fminf(tau * __fdividef(1.0f, s0), 1.0e18f);
         const float r1 = fminf(tau * __fdividef(1.0f, s1), 1.0e18f);
         const float r2 = fminf(tau * __fdividef(1.0f, s2), 1.0e18f);
@@ -320,9 +322,8 @@ __device__ __forceinline__ float phi_nf(float a, float b, float c, float d, floa
 // d = (1, 6, 3) enter the sum and the numerator by FMAs.
 template <int VAR>
 __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, double eps3, double &Nn, double &Dn) {
-    double I0, I1, I2, x0, y0, z0;
-    smoothness3<double>(a, b, c, d, I0, I1, I2, x0, y0, z0);
-    const double s0 = eps3 + I0, s1 = eps3 + I1, s2 = eps3 + I2;
+    double s0, s1, s2, x0, y0, z0;
+    smoothness3<double>(a, b, c, d, eps3, s0, s1, s2, x0, y0, z0);
     double W0, V1, V2;   // alpha_k / d_k times the common factor
     if constexpr (VAR == 0) {
         // alpha_k = d_k / s_k^2 times (s0 s1 s2)^2
@@ -334,7 +335,7 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
         // alpha_k = d_k (1 + tau^2 / s_k^2) times (s0 s1 s2)^2: with e_k =
         // s_k^2 and E = e0 e1 e2, (e_k + tau^2) prod_{j != k} e_j = E + tau^2
         // prod_{j != k} e_j, one FMA per weight
-        const double tau = fabs(I0 - I2);
+        const double tau = fabs(s0 - s2);   // |IS_0 - IS_2| / 3
         const double tt = tau * tau;
         const double e0 = s0 * s0, e1 = s1 * s1, e2 = s2 * s2;
         const double e12 = e1 * e2, e02 = e0 * e2, e01 = e0 * e1;
