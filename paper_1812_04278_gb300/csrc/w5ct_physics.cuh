@@ -298,22 +298,23 @@ template <int VAR>
 __device__ __forceinline__ float phi_nf(float a, float b, float c, float d, float eps3) {
     float s0, s1, s2, x0, y0, z0;
     smoothness3<float>(a, b, c, d, eps3, s0, s1, s2, x0, y0, z0);
-    float a0, a1, a2;
+    float e0, e1, e2;   // alpha_k / d_k
     if constexpr (VAR == 0) {
-        a0 = __fdividef(1.0f, s0 * s0);
-        a1 = 6.0f * __fdividef(1.0f, s1 * s1);
-        a2 = 3.0f * __fdividef(1.0f, s2 * s2);
+        e0 = __fdividef(1.0f, s0 * s0);
+        e1 = __fdividef(1.0f, s1 * s1);
+        e2 = __fdividef(1.0f, s2 * s2);
     } else {
         const float tau = fabsf(s0 - s2);   // |IS_0 - IS_2| / 3
         const float r0 = fminf(tau * __fdividef(1.0f, s0), 1.0e18f);
         const float r1 = fminf(tau * __fdividef(1.0f, s1), 1.0e18f);
         const float r2 = fminf(tau * __fdividef(1.0f, s2), 1.0e18f);
-        a0 = 1.0f + r0 * r0;
-        a1 = 6.0f * (1.0f + r1 * r1);
-        a2 = 3.0f * (1.0f + r2 * r2);
+        e0 = __fmaf_rn(r0, r0, 1.0f);
+        e1 = __fmaf_rn(r1, r1, 1.0f);
+        e2 = __fmaf_rn(r2, r2, 1.0f);
     }
-    const float inv = __fdividef(1.0f, (a0 + a1) + a2);
-    return (a0 * inv) * (x0 - y0) + __fmaf_rn(a2, 0.5f * inv, -0.25f) * (y0 - z0);
+    // D = e0 + 6 e1 + 3 e2; a_2 / 2 = 1.5 e2
+    const float inv = __fdividef(1.0f, __fmaf_rn(3.0f, e2, __fmaf_rn(6.0f, e1, e0)));
+    return (e0 * inv) * (x0 - y0) + __fmaf_rn(e2, 1.5f * inv, -0.25f) * (y0 - z0);
 }
 
 // double: the weights times the common factor (s_0 s_1 s_2)^2, so that no
@@ -466,12 +467,13 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
             const int qF = C_F0 + c;
             const Real f0 = SMQ(qF, 0), f1 = SMQ(qF, 1), f2 = SMQ(qF, 2), f3 = SMQ(qF, 3), f4 = SMQ(qF, 4),
                        f5 = SMQ(qF, 5);
-            X[0][c] = (Real(7) * (f2 + f3) - (f1 + f4)) * Real(1.0 / 12.0);
             X[1][c] = f1 - f0;
             X[2][c] = f2 - f1;
             X[3][c] = f3 - f2;
             X[4][c] = f4 - f3;
             X[5][c] = f5 - f4;
+            // (7 (f2 + f3) - (f1 + f4)) / 12 from the differences
+            X[0][c] = f2 + (Real(6) * X[3][c] + X[2][c] - X[4][c]) * Real(1.0 / 12.0);
             const int qU = c == 0 ? C_RHOQ : c == 1 ? C_MN : c == 2 ? C_MT1 : c == 3 ? C_MT2 : c == 4 ? C_BT1
                            : c == 5 ? C_BT2 : C_E;
             const Real u0 = SMQ(qU, 0), u1 = SMQ(qU, 1), u2 = SMQ(qU, 2), u3 = SMQ(qU, 3), u4 = SMQ(qU, 4),
