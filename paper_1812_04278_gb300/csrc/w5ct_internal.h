@@ -47,6 +47,15 @@ struct SweepTuning;
 #ifndef W5CT_F64_MINB
 #define W5CT_F64_MINB 1
 #endif
+// FP64 y- and z-sweeps: tiles of 16 pencils x 32 faces, whose cell box (37 x
+// 16 cells) stages 1.16 cells per face instead of the 1.31 of 32 x 16 (21 x
+// 32 cells); the x-sweep's 32 x 16 tile already stages 37 x 16.
+#ifndef W5CT_F64_BXYZ
+#define W5CT_F64_BXYZ 16
+#endif
+#ifndef W5CT_F64_T2YZ_NARROW
+#define W5CT_F64_T2YZ_NARROW 32
+#endif
 
 #ifndef W5CT_F32_FPT
 #define W5CT_F32_FPT 2
@@ -57,34 +66,37 @@ struct SweepTuning<float> {
 };
 template <>
 struct SweepTuning<double> {
-    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = W5CT_F64_MINB, FPT = W5CT_F64_T2X / 8;
+    static constexpr int T2X = W5CT_F64_T2X, T2YZ = W5CT_F64_T2YZ, MINB = W5CT_F64_MINB, FPT = W5CT_F64_T2X / 8,
+                         BXYZ = W5CT_F64_BXYZ;
 };
 
 template <int AX, typename Real>
 struct SweepCfg {
-    static constexpr int T2 = AX == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
+    static constexpr bool kNarrow = sizeof(Real) == 8 && AX != 0;   // FP64 y/z: 16 x 32
+    static constexpr int T2 = AX == 0 ? SweepTuning<Real>::T2X : kNarrow ? W5CT_F64_T2YZ_NARROW : SweepTuning<Real>::T2YZ;
+    static constexpr int BX = kNarrow ? W5CT_F64_BXYZ : 32;
     static constexpr int MINB = SweepTuning<Real>::MINB;
     static constexpr int FPT = SweepTuning<Real>::FPT;
-    using TT = SweepTile<AX, T2, 32, FPT>;
+    using TT = SweepTile<AX, T2, BX, FPT>;
     static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
 };
 
-// Single-patch sweep in tiles of 32 x T2 faces, FPT per thread (the block
-// is 32 x T2 / FPT threads).
-template <int AX, typename Real, int VAR, int T2, int MINB, int FPT>
+// Single-patch sweep in tiles of BX x T2 faces, FPT per thread (the block
+// is BX x T2 / FPT threads).
+template <int AX, typename Real, int VAR, int T2, int MINB, int FPT, int BX = 32>
 struct SinglePatchSweep {
-    using TT = SweepTile<AX, T2, 32, FPT>;
+    using TT = SweepTile<AX, T2, BX, FPT>;
     static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT>,
+        return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     static dim3 grid(int nx, int ny, int nz) {
-        if (AX == 0 || AX == 1) return dim3((nx + 31) / 32, (ny + TT::BY - 1) / TT::BY, nz);
-        return dim3((nx + 31) / 32, ny, (nz + TT::BZ - 1) / TT::BZ);
+        if (AX == 0 || AX == 1) return dim3((nx + BX - 1) / BX, (ny + TT::BY - 1) / TT::BY, nz);
+        return dim3((nx + BX - 1) / BX, ny, (nz + TT::BZ - 1) / TT::BZ);
     }
     static cudaError_t launch(const SweepArgs<Real> &a, cudaStream_t s) {
-        sweep_kernel<AX, Real, VAR, T2, MINB, FPT><<<grid(a.nx, a.ny, a.nz), dim3(32, TT::ROWS), smem, s>>>(a);
+        sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX><<<grid(a.nx, a.ny, a.nz), dim3(BX, TT::ROWS), smem, s>>>(a);
         return cudaGetLastError();
     }
 };
@@ -233,7 +245,7 @@ struct PersistentLaunch {
 template <int AX, typename Real, int VAR>
 cudaError_t prepare_sweep_axis() {
     using C = SweepCfg<AX, Real>;
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB, C::FPT>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, C::T2, C::MINB, C::FPT, C::BX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<Real, double>::value) {
@@ -338,23 +350,24 @@ cudaError_t launch_sweep_batched_impl(int axis, int variant, int tv, const Sweep
 // always uses its default tile.
 constexpr int kSmallTileHeights[2] = {8, 4};
 
-// blocks of the single-patch sweep along `axis` in tiles t2 high
-inline long long sweep_blocks(int axis, int t2, int nx, int ny, int nz) {
-    const long long bx = (nx + 31) / 32;
-    if (axis == 2) return bx * ny * ((nz + t2 - 1) / t2);
-    return bx * ((ny + t2 - 1) / t2) * nz;     // x- and y-sweeps: t2 pencils or faces along y
+// blocks of the single-patch sweep along `axis` in tiles of bx lanes x t2
+inline long long sweep_blocks(int axis, int t2, int bx, int nx, int ny, int nz) {
+    const long long nbx = (nx + bx - 1) / bx;
+    if (axis == 2) return nbx * ny * ((nz + t2 - 1) / t2);
+    return nbx * ((ny + t2 - 1) / t2) * nz;     // x- and y-sweeps: t2 pencils or faces along y
 }
 
 // Tile height of the single-patch sweep along `axis`: the default, or for
-// FP64 the tallest of the shorter tiles that gives every SM at least two
-// blocks (the shortest if none does).
+// FP64 the tallest of the shorter (32-lane) tiles that gives every SM at
+// least two blocks (the shortest if none does).
 template <typename Real>
 inline int choose_sweep_t2(int axis, int nx, int ny, int nz, int sms) {
-    const int t2d = axis == 0 ? SweepTuning<Real>::T2X : SweepTuning<Real>::T2YZ;
+    const int t2d = axis == 0 ? SweepCfg<0, Real>::T2 : SweepCfg<1, Real>::T2;
+    const int bxd = axis == 0 ? SweepCfg<0, Real>::BX : SweepCfg<1, Real>::BX;
     if (!std::is_same<Real, double>::value) return t2d;
-    if (sweep_blocks(axis, t2d, nx, ny, nz) >= 2LL * sms) return t2d;
+    if (sweep_blocks(axis, t2d, bxd, nx, ny, nz) >= 2LL * sms) return t2d;
     for (int h : kSmallTileHeights)
-        if (sweep_blocks(axis, h, nx, ny, nz) >= 2LL * sms) return h;
+        if (sweep_blocks(axis, h, 32, nx, ny, nz) >= 2LL * sms) return h;
     return kSmallTileHeights[1];
 }
 
@@ -367,7 +380,7 @@ cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) 
     }
     if (t2 != 0 && t2 != C::T2) return cudaErrorInvalidValue;
     // the default tile; its shared memory is allowed by prepare_sweeps() at w5ct_init_grid
-    return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::FPT>::launch(a, s);
+    return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::FPT, C::BX>::launch(a, s);
 }
 
 template <typename Real>

@@ -263,17 +263,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const Patch
     sweep_tile_at<AX, Real, VAR, T2, BX, FPT, SB>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
 }
 
-// One tile per block over a single patch: 32 x T2 / FPT threads (at most
+// One tile per block over a single patch: BX x T2 / FPT threads (at most
 // 256), FPT faces per thread.
-template <int AX, typename Real, int VAR, int T2, int MINB, int FPT = T2 / 8>
-__global__ void __launch_bounds__(SweepTile<AX, T2, 32, FPT>::NT, MINB) sweep_kernel(SweepArgs<Real> a) {
+template <int AX, typename Real, int VAR, int T2, int MINB, int FPT = T2 / 8, int BX = 32>
+__global__ void __launch_bounds__(SweepTile<AX, T2, BX, FPT>::NT, MINB) sweep_kernel(SweepArgs<Real> a) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     PatchGeom pg;
     pg.nx = a.nx;
     pg.ny = a.ny;
     pg.nz = a.nz;
     pg.off = 0;
-    sweep_tile<AX, Real, VAR, T2, 32, FPT>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z,
+    sweep_tile<AX, Real, VAR, T2, BX, FPT>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z,
                                           reinterpret_cast<Real *>(w5ct_smem));
 }
 
