@@ -171,10 +171,11 @@ __device__ __forceinline__ void cell_fill_frame(Real *sm, int stride, Real rho, 
     sm[C_MT1 * stride] = m1;
     sm[C_MT2 * stride] = m2;
     sm[C_E * stride] = E;
-    sm[C_F0 * stride] = r * vn;
-    sm[C_F1 * stride] = r * vn * vn + Pt - Bn * Bn;
-    sm[C_F2 * stride] = r * vn * v1 - Bn * B1;
-    sm[C_F3 * stride] = r * vn * v2 - Bn * B2;
+    // rho v_n = m_n (v = m / rho with the same, possibly floored, rho)
+    sm[C_F0 * stride] = mn;
+    sm[C_F1 * stride] = mn * vn + Pt - Bn * Bn;
+    sm[C_F2 * stride] = mn * v1 - Bn * B1;
+    sm[C_F3 * stride] = mn * v2 - Bn * B2;
     sm[C_F4 * stride] = B1 * vn - Bn * v1;
     sm[C_F5 * stride] = B2 * vn - Bn * v2;
     sm[C_F6 * stride] = (E + Pt) * vn - Bn * vB;
@@ -184,7 +185,7 @@ __device__ __forceinline__ void cell_fill_frame(Real *sm, int stride, Real rho, 
     Real fmc, cms, cf2, csl2;
     speeds<Real>(cs2, ca2, bt2, fmc, cms, cf2, csl2);
     sm[C_CF * stride] = m::sqrt_(cf2);
-    sm[C_CA * stride] = m::abs_(Bn) * (m::sqrt_(r) * ir);     // |B_n| / sqrt(rho)
+    sm[C_CA * stride] = m::abs_(Bn) * m::rsqrt_(r);     // |B_n| / sqrt(rho)
     sm[C_CSL * stride] = m::sqrt_(csl2);
 }
 
