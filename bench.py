@@ -197,7 +197,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "6a00098ff34f89bf", "fp64": 103.39, "fp32": 44.33}
+SWEEP_TRAFFIC = {"src": "d062f23e54243882", "fp64": 103.58, "fp32": 44.41}
 
 
 def hbm_gbs(traffic, launch_ms):
