@@ -188,7 +188,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_sweep32.cu", "w5ct_sweep64.cu"):
+    for f in ("w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_sweep32.cu", "w5ct_sweep64.cu",
+              "w5ct_sweep64dw.cu"):
         h.update(open(os.path.join(ROOT, "paper_1812_04278_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -197,7 +198,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "d062f23e54243882", "fp64": 103.58, "fp32": 44.41}
+SWEEP_TRAFFIC = {"src": "d0a6eb31f311821e", "fp64": 103.57, "fp32": 43.81, "fp64dw": 105.17}
 
 
 def hbm_gbs(traffic, launch_ms):
@@ -207,7 +208,7 @@ def hbm_gbs(traffic, launch_ms):
 
 
 def sweep_traffic(key, zones):
-    if SWEEP_TRAFFIC.get("src") != kernel_source_hash():
+    if SWEEP_TRAFFIC.get("src") != kernel_source_hash() or key not in SWEEP_TRAFFIC:
         return None
     return SWEEP_TRAFFIC[key] * zones
 
@@ -380,6 +381,24 @@ def run_native(args):
     drift64 = conservation_drift(s64, cons, bface, dx)
     s64.close()
 
+    # ---- FP64 with the WENO part in double-word arithmetic: timed like the
+    # FP64 run, then its deviation from the FP64 state at the FP64 run's dt
+    # sequence
+    sdw, msdw, nswdw, swmsdw, launchesdw, _ = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP64_DW,
+                                                        args.steps, args.warmup, None, None, barrier)
+    msdw = max_over_ranks(msdw)
+    sdw.set_state(cons_d, bface_d)
+    for k in range(nlog):
+        w5.w5ct_step_dev(sdw.ctx, dt_log[k:k + 1])
+    cdw = torch.empty_like(cons_d)
+    bdw = torch.empty_like(bface_d)
+    w5.w5ct_get_state(sdw.ctx, cdw, bdw, None, 1)
+    divbdw = sdw.div_b_norm()[0]
+    sdw.close()
+    reldw = float(max((cdw - c64).abs().max().item(), (bdw - b64).abs().max().item()) /
+                  max(c64.abs().max().item(), b64.abs().max().item()))
+    del cdw, bdw
+
     # ---- FP32-bulk
     s32, ms32, nsw32, swms32, launches32, _ = timed_run(torch, w5, shape, dx, cons_d, bface_d, w5.W5CT_FP32_BULK,
                                                         args.steps, args.warmup, None, None, barrier)
@@ -446,6 +465,8 @@ def run_native(args):
     sweep_flops = SWEEP_FLOPS_PER_ZONE[1] * zones
     ach64 = sweep_flops / (swms64 / nsw64 * 1e-3) / 1e12
     ach32 = sweep_flops / (swms32 / nsw32 * 1e-3) / 1e12
+    achdw = sweep_flops / (swmsdw / nswdw * 1e-3) / 1e12
+    valuedw = replica_throughput(world, zones, args.steps, msdw)
     line = {
         "metric": "zone-updates/s (3D WENO5-CT MHD, full RK4 step)",
         "value": value64,
@@ -482,6 +503,19 @@ def run_native(args):
                          "step_tflops": STEP_FLOPS_PER_ZONE[1] * value32 / world / 1e12,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "gpu_launches": launches32,
+        },
+        "fp64_dw": {
+            "value": valuedw, "unit": "zone-updates/s", "ms_per_step": msdw / args.steps,
+            "dtype": "f64; WENO split, weights and interpolants in double-word f32 pairs (48-bit significand)",
+            "speedup_vs_fp64": valuedw / value64, "max_rel_vs_fp64": reldw, "error_steps": nlog,
+            "div_b_linf": divbdw,
+            "roofline": {"kernel": "sweep_kernel (FP64, double-word WENO)", "bound": "alu", "achieved": achdw,
+                         "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achdw / PEAK_FP64_TFLOPS,
+                         "traffic": sweep_traffic("fp64dw", zones), "launch_ms": swmsdw / nswdw,
+                         "hbm_gbs": hbm_gbs(sweep_traffic("fp64dw", zones), swmsdw / nswdw),
+                         "note": "the WENO part runs on the FP32 pipe, so the FP64 unit-count peak does not "
+                                 "bound this kernel; frac compares it with the FP64-only form's ceiling"},
+            "gpu_launches": launchesdw,
         },
         "weno_js": {"fp64_value": replica_throughput(world, zones, args.steps, msjs),
                     "fp64_ms_per_step": msjs / args.steps,

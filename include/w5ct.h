@@ -61,6 +61,15 @@ extern "C" {
                                       RK stage accumulation, CT EMF accumulation
                                       into the face field and all reductions in
                                       double */
+#define W5CT_FP64_DW 2             /* W5CT_FP64 with the WENO part of each
+                                      characteristic field's flux (LF split,
+                                      smoothness indicators, nonlinear weights,
+                                      interpolants; Sec. 2.2) in double-word
+                                      arithmetic (pairs of floats, 48-bit
+                                      significand) on the FP32 pipe, in the
+                                      single-patch sweeps of the default tiles;
+                                      everything else, every stored value and
+                                      every other kernel as W5CT_FP64 */
 
 typedef struct w5ct_ctx w5ct_ctx;
 
@@ -68,7 +77,7 @@ typedef struct {
     double gamma;        /* adiabatic index (5/3 in the paper's tests) */
     double cfl;          /* Courant number of Eq. (cfl) (0.8 in the paper) */
     int weno_variant;    /* W5CT_WENO_JS or W5CT_WENO_Z */
-    int precision;       /* W5CT_FP64 or W5CT_FP32_BULK */
+    int precision;       /* W5CT_FP64, W5CT_FP32_BULK or W5CT_FP64_DW */
     double eps_js;       /* JS epsilon, 1e-6 (Sec. 2.2) */
     double eps_z;        /* WENO-Z epsilon, 1e-40 (Sec. 2.2); FP32_BULK uses
                             max(eps_z, 1e-30) because 1e-40 is subnormal in float */

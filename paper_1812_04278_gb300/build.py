@@ -13,7 +13,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libw5ct.so")
 SOURCES = ["w5ct_adjoint64z.cu", "w5ct_adjoint64js.cu", "w5ct_adjoint32z.cu", "w5ct_adjoint32js.cu",
-           "w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_fused32.cu", "w5ct_fused64.cu",
+           "w5ct_api.cu", "w5ct_sweep32.cu", "w5ct_sweep64.cu", "w5ct_sweep64dw.cu", "w5ct_fused32.cu",
+           "w5ct_fused64.cu",
            "w5ct_noalloc.cu"]
 HEADERS = ["w5ct_physics.cuh", "w5ct_kernels.cuh", "w5ct_internal.h", "w5ct_adjoint.cuh",
            "w5ct_fused.cuh"]

@@ -94,6 +94,9 @@ struct w5ct_ctx {
 
 namespace {
 
+// state, fluxes and every kernel in double (W5CT_FP64 and W5CT_FP64_DW)
+inline bool ctx_fp64(const w5ct_ctx *c) { return c->cfg.precision != W5CT_FP32_BULK; }
+
 int fail(w5ct_ctx *c, int code, const char *fmt, ...) {
     char *buf = c ? c->err : g_create_err;
     va_list ap;
@@ -168,11 +171,11 @@ PatchGeom patch_of(const w5ct_ctx *c, int p) { return c->pg[p]; }
 dim3 cell_grid(const w5ct_ctx *c) { return dim3((c->nx + 31) / 32, (c->ny + 7) / 8, c->nz); }
 
 int n_variants(const w5ct_ctx *c) {
-    return c->cfg.precision == W5CT_FP64 ? num_tile_variants<double>() : num_tile_variants<float>();
+    return ctx_fp64(c) ? num_tile_variants<double>() : num_tile_variants<float>();
 }
 
 void variant_shape(const w5ct_ctx *c, int axis, int v, int &bx, int &t2) {
-    if (c->cfg.precision == W5CT_FP64)
+    if (ctx_fp64(c))
         tile_shape<double>(axis, v, bx, t2);
     else
         tile_shape<float>(axis, v, bx, t2);
@@ -382,7 +385,7 @@ int build_fused(w5ct_ctx *c) {
     if (c->fused_buf) return W5CT_OK;
     std::vector<int4> items;
     std::vector<int> ncb(c->npatch), ntile(c->npatch, 0);
-    const bool fp64 = c->cfg.precision == W5CT_FP64;
+    const bool fp64 = ctx_fp64(c);
     for (int p = 0; p < c->npatch; ++p) {
         const PatchGeom &g = c->pg[p];
         ncb[p] = (int)(((long long)g.nx * g.ny * g.nz + kFusedCells - 1) / kFusedCells);
@@ -553,7 +556,7 @@ int fused_step_impl(w5ct_ctx *c, const double *dts_in, double *dts_out, bool che
 }
 
 int fused_step(w5ct_ctx *c, const double *dts_in, double *dts_out) {
-    return c->cfg.precision == W5CT_FP64 ? fused_step_impl<double>(c, dts_in, dts_out)
+    return ctx_fp64(c) ? fused_step_impl<double>(c, dts_in, dts_out)
                                          : fused_step_impl<float>(c, dts_in, dts_out);
 }
 
@@ -607,6 +610,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
     a.K = make_phys<Real>(c->cfg);
     a.flag = c->flag;
     a.hits = c->hits;
+    a.dw = c->cfg.precision == W5CT_FP64_DW;
 
     const UpdateArgs<Real> u = update_args<Real>(c, dt_dev);
 
@@ -662,7 +666,7 @@ int run_step(w5ct_ctx *c, const double *dt_dev, bool cellb_done, int last_stage 
 }
 
 int step_impl(w5ct_ctx *c, const double *dt_dev, bool cellb_done) {
-    if (c->cfg.precision == W5CT_FP64) return run_step<double>(c, dt_dev, cellb_done);
+    if (ctx_fp64(c)) return run_step<double>(c, dt_dev, cellb_done);
     return run_step<float>(c, dt_dev, cellb_done);
 }
 
@@ -683,9 +687,9 @@ int read_flag(w5ct_ctx *c, int *flag_out) {
 
 // S_d of every patch into out[3 p + d] (host, 3 * npatch doubles)
 int speeds_impl(w5ct_ctx *c, double *out) {
-    int rc = c->cfg.precision == W5CT_FP64 ? launch_cellb<double>(c) : launch_cellb<float>(c);
+    int rc = ctx_fp64(c) ? launch_cellb<double>(c) : launch_cellb<float>(c);
     if (rc) return rc;
-    rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
+    rc = ctx_fp64(c) ? launch_speed<double>(c) : launch_speed<float>(c);
     if (rc) return rc;
     std::vector<unsigned long long> bits(3 * (size_t)c->npatch);
     W5_CUDA(c, cudaMemcpyAsync(bits.data(), c->smax, bits.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
@@ -731,7 +735,7 @@ int w5ct_create(const w5ct_config *cfg, w5ct_ctx **out) {
     if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return fail(nullptr, W5CT_ERR_ARG, "gamma must be > 1 and cfl > 0");
     if (cfg->weno_variant != W5CT_WENO_JS && cfg->weno_variant != W5CT_WENO_Z)
         return fail(nullptr, W5CT_ERR_ARG, "unknown weno_variant %d", cfg->weno_variant);
-    if (cfg->precision != W5CT_FP64 && cfg->precision != W5CT_FP32_BULK)
+    if (cfg->precision != W5CT_FP64 && cfg->precision != W5CT_FP32_BULK && cfg->precision != W5CT_FP64_DW)
         return fail(nullptr, W5CT_ERR_ARG, "unknown precision %d", cfg->precision);
     if (!(cfg->eps_js > 0.0) || !(cfg->eps_z > 0.0) || !(cfg->eps_b > 0.0))
         return fail(nullptr, W5CT_ERR_ARG, "epsilons must be positive");
@@ -741,7 +745,7 @@ int w5ct_create(const w5ct_config *cfg, w5ct_ctx **out) {
     if (!c) return fail(nullptr, W5CT_ERR_ARG, "out of host memory");
     c->cfg = *cfg;
     c->stream = (cudaStream_t)cfg->stream;
-    c->real_size = cfg->precision == W5CT_FP64 ? sizeof(double) : sizeof(float);
+    c->real_size = cfg->precision == W5CT_FP32_BULK ? sizeof(float) : sizeof(double);
     snprintf(c->err, sizeof(c->err), "no error");
     *out = c;
     return W5CT_OK;
@@ -823,7 +827,7 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
     const size_t o_qs = take(5 * n * rs), o_bs = take(3 * n * rs), o_bc = take(3 * n * rs);
     const size_t o_Fx = take(5 * n * rs), o_Fy = take(5 * n * rs), o_Fz = take(5 * n * rs);
     const size_t o_Sx = take(2 * n * rs), o_Sy = take(2 * n * rs), o_Sz = take(2 * n * rs);
-    const bool fp32 = c->cfg.precision != W5CT_FP64;
+    const bool fp32 = !ctx_fp64(c);
     const size_t o_q0r = fp32 ? take(5 * n * rs) : 0, o_b0r = fp32 ? take(3 * n * rs) : 0;
     const size_t np = (size_t)npatch;
     const size_t o_dt = take(8 * np), o_smax = take(24 * np), o_flag = take(4), o_hits = take(8);
@@ -869,18 +873,18 @@ int w5ct_init_grid(w5ct_ctx *c, int npatch, const int *n3, const double *dx3) {
         int rc = build_tiles(c);
         if (rc) return rc;
     }
-    W5_CUDA(c, c->cfg.precision == W5CT_FP64 ? prepare_sweeps<double>() : prepare_sweeps<float>());
+    W5_CUDA(c, ctx_fp64(c) ? prepare_sweeps<double>() : prepare_sweeps<float>());
     {
         int dev = 0, sms = 0;
         W5_CUDA(c, cudaGetDevice(&dev));
         W5_CUDA(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         for (int ax = 0; ax < 3; ++ax)
-            c->sweep_t2[ax] = c->cfg.precision == W5CT_FP64 ? choose_sweep_t2<double>(ax, c->nx, c->ny, c->nz, sms)
+            c->sweep_t2[ax] = ctx_fp64(c) ? choose_sweep_t2<double>(ax, c->nx, c->ny, c->nz, sms)
                                                             : choose_sweep_t2<float>(ax, c->nx, c->ny, c->nz, sms);
     }
     c->schedule = 0;
     for (int v = 0; v < n_variants(c); ++v) {
-        const cudaError_t eg = c->cfg.precision == W5CT_FP64 ? persistent_grid<double>(c->cfg.weno_variant, v, c->pgrid[v])
+        const cudaError_t eg = ctx_fp64(c) ? persistent_grid<double>(c->cfg.weno_variant, v, c->pgrid[v])
                                                              : persistent_grid<float>(c->cfg.weno_variant, v, c->pgrid[v]);
         W5_CUDA(c, eg);
     }
@@ -909,7 +913,7 @@ int w5ct_set_state(w5ct_ctx *c, int patch, const double *cons, const double *bfa
         for (int f = 0; f < 3; ++f)
             W5_CUDA(c, cudaMemcpyAsync(c->b0 + f * n + off, bface + f * np, np * sizeof(double), kind, c->stream));
     }
-    if (c->cfg.precision == W5CT_FP64) {
+    if (ctx_fp64(c)) {
         for (int f = 0; f < 5; ++f)
             W5_CUDA(c, cudaMemcpyAsync((double *)c->qs + f * n + off, c->q0 + f * n + off, np * 8,
                                        cudaMemcpyDeviceToDevice, c->stream));
@@ -999,9 +1003,9 @@ int w5ct_step_cfl(w5ct_ctx *c, double *dt_dev_out) {
     int rc = check_ready(c);
     if (rc) return rc;
     if (c->npatch > 1 && c->schedule == 2) return fused_step(c, nullptr, dt_dev_out);
-    rc = c->cfg.precision == W5CT_FP64 ? launch_cellb<double>(c) : launch_cellb<float>(c);
+    rc = ctx_fp64(c) ? launch_cellb<double>(c) : launch_cellb<float>(c);
     if (rc) return rc;
-    rc = c->cfg.precision == W5CT_FP64 ? launch_speed<double>(c) : launch_speed<float>(c);
+    rc = ctx_fp64(c) ? launch_speed<double>(c) : launch_speed<float>(c);
     if (rc) return rc;
     rc = launch_dt(c, dt_dev_out);
     if (rc) return rc;
@@ -1102,6 +1106,7 @@ SweepArgs<Real> sweep_args(w5ct_ctx *c, int ax) {
     a.K = make_phys<Real>(c->cfg);
     a.flag = c->flag;
     a.hits = c->hits;
+    a.dw = c->cfg.precision == W5CT_FP64_DW;
     return a;
 }
 
@@ -1193,7 +1198,7 @@ int autotune_measure(w5ct_ctx *c, int reps) {
     const bool timing = c->timing;
     c->timing = false;
     const size_t n = (size_t)c->n, rs = c->real_size;
-    const bool fp32 = c->cfg.precision != W5CT_FP64;
+    const bool fp32 = !ctx_fp64(c);
     const size_t bq = 8 * n * 8, br = 8 * n * rs, bsnap = bq + br + (fp32 ? br : 0);
     char *snap = nullptr;
     if (cudaMalloc(&snap, bsnap) == cudaSuccess) {
@@ -1367,7 +1372,7 @@ int w5ct_autotune(w5ct_ctx *c, int mode, int reps) {
                     nv - 1);
     if (mode == W5CT_TUNE_MEASURE) {
         if (reps < 1 || reps > 100) return fail(c, W5CT_ERR_ARG, "reps must be in 1 .. 100");
-        return c->cfg.precision == W5CT_FP64 ? autotune_measure<double>(c, reps) : autotune_measure<float>(c, reps);
+        return ctx_fp64(c) ? autotune_measure<double>(c, reps) : autotune_measure<float>(c, reps);
     }
     if (mode == W5CT_TUNE_MODEL) {
         default_variants(c);
@@ -1406,7 +1411,7 @@ int w5ct_fused_wait_check(w5ct_ctx *c, long long spin_limit, int *status) {
     int flag0 = 0;
     rc = read_flag(c, &flag0);
     if (rc) return rc;
-    rc = c->cfg.precision == W5CT_FP64 ? fused_step_impl<double>(c, nullptr, nullptr, true, spin_limit)
+    rc = ctx_fp64(c) ? fused_step_impl<double>(c, nullptr, nullptr, true, spin_limit)
                                        : fused_step_impl<float>(c, nullptr, nullptr, true, spin_limit);
     if (rc) return rc;
     int flag = 0;
@@ -1445,7 +1450,7 @@ int w5ct_adjoint_step(w5ct_ctx *c, double dt, const double *lam_q, const double 
     if (c->npatch != 1) return fail(c, W5CT_ERR_UNSUPPORTED, "the adjoint step takes one patch");
     if (!(dt > 0.0) || !(dt < 1e300)) return fail(c, W5CT_ERR_ARG, "dt must be finite and > 0 (got %g)", dt);
     if (!lam_q || !lam_b || !lam_q_out || !lam_b_out) return fail(c, W5CT_ERR_ARG, "null adjoint buffer");
-    return c->cfg.precision == W5CT_FP64 ? adjoint_step_impl<double>(c, dt, lam_q, lam_b, lam_q_out, lam_b_out)
+    return ctx_fp64(c) ? adjoint_step_impl<double>(c, dt, lam_q, lam_b, lam_q_out, lam_b_out)
                                           : adjoint_step_impl<float>(c, dt, lam_q, lam_b, lam_q_out, lam_b_out);
 }
 

@@ -17,6 +17,13 @@ void set_global_error(const char *text);
 template <typename Real>
 cudaError_t launch_sweep(int axis, int variant, int t2, const SweepArgs<Real> &a, cudaStream_t s);
 
+// The FP64 single-patch sweeps of the default tiles with the WENO part of
+// every flux in double-word arithmetic (launch_sweep takes them when a.dw is
+// set and the tile is the default one), and the shared-memory allowance of
+// their kernels.  Defined in w5ct_sweep64dw.cu.
+cudaError_t launch_sweep_f64dw(int axis, int variant, const SweepArgs<double> &a, cudaStream_t s);
+cudaError_t prepare_sweeps_f64dw();
+
 // Sweep tiling per arithmetic type: faces per block in the second tile
 // direction (x-sweep: pencils along y; y- and z-sweeps: faces along the
 // axis) and the minimum resident blocks per SM the register budget targets.
@@ -83,12 +90,12 @@ struct SweepCfg {
 
 // Single-patch sweep in tiles of BX x T2 faces, FPT per thread (the block
 // is BX x T2 / FPT threads).
-template <int AX, typename Real, int VAR, int T2, int MINB, int FPT, int BX = 32>
+template <int AX, typename Real, int VAR, int T2, int MINB, int FPT, int BX = 32, bool DW = false>
 struct SinglePatchSweep {
     using TT = SweepTile<AX, T2, BX, FPT>;
     static constexpr size_t smem = (size_t)TT::NC * box_quantities<Real>() * sizeof(Real);
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX>,
+        return cudaFuncSetAttribute(sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX, DW>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     static dim3 grid(int nx, int ny, int nz) {
@@ -96,7 +103,7 @@ struct SinglePatchSweep {
         return dim3((nx + BX - 1) / BX, ny, (nz + TT::BZ - 1) / TT::BZ);
     }
     static cudaError_t launch(const SweepArgs<Real> &a, cudaStream_t s) {
-        sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX><<<grid(a.nx, a.ny, a.nz), dim3(BX, TT::ROWS), smem, s>>>(a);
+        sweep_kernel<AX, Real, VAR, T2, MINB, FPT, BX, DW><<<grid(a.nx, a.ny, a.nz), dim3(BX, TT::ROWS), smem, s>>>(a);
         return cudaGetLastError();
     }
 };
@@ -272,6 +279,8 @@ cudaError_t prepare_sweep_axis() {
 template <typename Real>
 cudaError_t prepare_sweeps_impl() {
     cudaError_t e;
+    if constexpr (std::is_same<Real, double>::value)
+        if ((e = prepare_sweeps_f64dw()) != cudaSuccess) return e;
     if ((e = prepare_sweep_axis<0, Real, 0>()) != cudaSuccess) return e;
     if ((e = prepare_sweep_axis<1, Real, 0>()) != cudaSuccess) return e;
     if ((e = prepare_sweep_axis<2, Real, 0>()) != cudaSuccess) return e;
@@ -379,6 +388,8 @@ cudaError_t launch_sweep_axis(int t2, const SweepArgs<Real> &a, cudaStream_t s) 
         if (t2 == 4) return SinglePatchSweep<AX, Real, VAR, 4, C::MINB, 1>::launch(a, s);
     }
     if (t2 != 0 && t2 != C::T2) return cudaErrorInvalidValue;
+    if constexpr (std::is_same<Real, double>::value)
+        if (a.dw) return launch_sweep_f64dw(AX, VAR, a, s);
     // the default tile; its shared memory is allowed by prepare_sweeps() at w5ct_init_grid
     return SinglePatchSweep<AX, Real, VAR, C::T2, C::MINB, C::FPT, C::BX>::launch(a, s);
 }

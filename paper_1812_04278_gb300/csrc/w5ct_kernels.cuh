@@ -36,6 +36,7 @@ struct SweepArgs {
     Phys<Real> K;
     int *flag;
     unsigned long long *hits;
+    int dw = 0;   // host-side choice: FP64 single-patch sweeps with the double-word WENO
 };
 
 // Cells whose loads a thread of a single-axis sweep kernel issues together
@@ -80,7 +81,7 @@ struct PatchGeom {
 // computed by the block's NT threads, numbered (tx, ty) in [0, BX) x
 // [0, ROWS).  sm: shared memory of box_quantities<Real>() * NC elements.  SB: cells whose loads
 // a thread issues together when it stages the cell box.
-template <int AX, typename Real, int VAR, int T2, int BX, int FPT, int SB = kStageBatch>
+template <int AX, typename Real, int VAR, int T2, int BX, int FPT, int SB = kStageBatch, bool DWW = false>
 __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
                                               Real *sm, int tx, int ty) {
     using TT = SweepTile<AX, T2, BX, FPT>;
@@ -163,7 +164,7 @@ __device__ __forceinline__ void sweep_tile_at(const SweepArgs<Real> &a, const Pa
         if (gx < nx && gy < ny && gz < nz) {
             const int c0 = bx + TT::CX * (by + TT::CY * bz);   // stencil cell i-2
             Real Ff[7], s1, s2;
-            face_flux<Real, VAR, box_diff<Real>()>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
+            face_flux<Real, VAR, box_diff<Real>(), DWW>(sm + c0, TT::NC, TT::ST, a.K, Ff, s1, s2);
             const size_t g = off + (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * (size_t)gz);
             a.F[0][g] = Ff[0];
             a.F[1 + AX][g] = Ff[1];
@@ -257,15 +258,17 @@ __device__ __forceinline__ void sweep_tile_rt(const SweepArgs<Real> &a, const Pa
 }
 
 // One tile computed by the whole block, blockDim = (BX, ROWS).
-template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8, int SB = kStageBatch>
+template <int AX, typename Real, int VAR, int T2, int BX = 32, int FPT = T2 / 8, int SB = kStageBatch,
+          bool DWW = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs<Real> &a, const PatchGeom &pg, int tbx, int tby, int tbz,
                                            Real *sm) {
-    sweep_tile_at<AX, Real, VAR, T2, BX, FPT, SB>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
+    sweep_tile_at<AX, Real, VAR, T2, BX, FPT, SB, DWW>(a, pg, tbx, tby, tbz, sm, (int)threadIdx.x, (int)threadIdx.y);
 }
 
 // One tile per block over a single patch: BX x T2 / FPT threads (at most
-// 256), FPT faces per thread.
-template <int AX, typename Real, int VAR, int T2, int MINB, int FPT = T2 / 8, int BX = 32>
+// 256), FPT faces per thread.  DW (double only): the WENO part of every
+// field's flux in double-word arithmetic (weno_field).
+template <int AX, typename Real, int VAR, int T2, int MINB, int FPT = T2 / 8, int BX = 32, bool DW = false>
 __global__ void __launch_bounds__(SweepTile<AX, T2, BX, FPT>::NT, MINB) sweep_kernel(SweepArgs<Real> a) {
     extern __shared__ __align__(16) unsigned char w5ct_smem[];
     PatchGeom pg;
@@ -273,8 +276,8 @@ __global__ void __launch_bounds__(SweepTile<AX, T2, BX, FPT>::NT, MINB) sweep_ke
     pg.ny = a.ny;
     pg.nz = a.nz;
     pg.off = 0;
-    sweep_tile<AX, Real, VAR, T2, BX, FPT>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z,
-                                          reinterpret_cast<Real *>(w5ct_smem));
+    sweep_tile<AX, Real, VAR, T2, BX, FPT, kStageBatch, DW>(a, pg, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                            reinterpret_cast<Real *>(w5ct_smem));
 }
 
 // Tile tables hold int4 (patch | axis << 28, tile x, tile y, tile z).

@@ -363,6 +363,156 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
     Nn = W0 * (x0 - y0) + fma(1.5, V2, -0.25 * Dn) * (y0 - z0);
 }
 
+// ---------------------------------------------------------------- double-word
+// A double-word number is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2: 48 significand bits (unit roundoff u^2, u = 2^-24)
+// and float's exponent range.  Each operation is a short sequence of FP32
+// operations built on the error-free transforms TwoSum (Knuth), Fast2Sum
+// (Dekker; |a| >= |b|) and TwoProd (one FMA), as analysed by Joldes, Muller
+// and Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic", ACM TOMS 44(2), 2017.  The intrinsics keep every
+// step a separately rounded operation (no contraction into FMAs).
+struct dw {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dw ef_fast2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dw ef_twosum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    return {s, __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv))};
+}
+__device__ __forceinline__ dw ef_twoprod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// x + y for operands of any sign (relative error below 3 u^2)
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+    const dw s = ef_twosum(x.hi, y.hi);
+    const dw t = ef_twosum(x.lo, y.lo);
+    const dw v = ef_fast2sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return ef_fast2sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+// x + y for operands of one sign (no cancellation; relative error ~ 2 u^2)
+__device__ __forceinline__ dw dw_add_same(dw x, dw y) {
+    const dw s = ef_twosum(x.hi, y.hi);
+    return ef_fast2sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+// x * y with y a float, and with y a double-word
+__device__ __forceinline__ dw dw_mul_f(dw x, float y) {
+    const dw c = ef_twoprod(x.hi, y);
+    return ef_fast2sum(c.hi, __fmaf_rn(x.lo, y, c.lo));
+}
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+    const dw c = ef_twoprod(x.hi, y.hi);
+    const float t = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+    return ef_fast2sum(c.hi, __fadd_rn(c.lo, t));
+}
+// x / y: the float quotient q from a reciprocal refined by one Newton step,
+// the residual x - y q in double-word, and its quotient as the correction
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y.hi));
+    r = __fmaf_rn(r, __fmaf_rn(-y.hi, r, 1.0f), r);
+    const float q = __fmul_rn(x.hi, r);
+    const dw yq = dw_mul_f(y, q);
+    const dw p = ef_twosum(x.hi, -yq.hi);
+    const float d = __fadd_rn(p.hi, __fadd_rn(__fsub_rn(p.lo, yq.lo), x.lo));
+    return ef_fast2sum(q, __fmul_rn(d, r));
+}
+__device__ __forceinline__ bool dw_eq(dw x, dw y) { return x.hi == y.hi && x.lo == y.lo; }
+
+// A double as a double-word on the integer pipes (IEEE 754 binary64 layout:
+// exponent bias 1023, 52 fraction bits): hi is x truncated to 24 significand
+// bits, lo the remaining 29 bits rounded to 24, then renormalised (Fast2Sum).
+// |x| below 2^-126 gives 0, |x| at or above 2^128 gives +-inf: neither
+// occurs for the WENO inputs of a physical state, whose relative precision
+// here is 2^-48.
+__device__ __forceinline__ dw dw_from_double(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const unsigned sgn = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7ffu);
+    const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29);
+    const float m = __uint2float_rn(lw & 0x1fffffffu);
+    const float lo = __fmul_rn(m, __uint_as_float((unsigned)(e - 948) << 23));   // m 2^(e - 1075)
+    float h = __uint_as_float(hb), l = __uint_as_float(__float_as_uint(lo) | sgn);
+    if (e <= 948) l = 0.0f;
+    if (e <= 896) h = 0.0f;
+    if (e >= 1151) {
+        h = __uint_as_float(sgn | 0x7f800000u);
+        l = 0.0f;
+    }
+    return ef_fast2sum(h, l);
+}
+
+// A float as the double of equal value on the integer pipes (binary32:
+// bias 127, 23 fraction bits); zeros and subnormals give 0, infinities and
+// NaNs a NaN.
+__device__ __forceinline__ double dw_f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned ef = (b >> 23) & 0xffu;
+    const unsigned hw = (b & 0x80000000u) | ((ef + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    double d = __hiloint2double((int)hw, (int)(b << 29));
+    if (ef == 0u) d = 0.0;
+    if (ef == 0xffu) d = __longlong_as_double(0x7ff8000000000000LL);
+    return d;
+}
+
+// phi_N (Sec. 2.2) of four double-word stencil differences (eps3 as in
+// smoothness3), returned as 3 phi_N = (e_0 / D) t1 + (3 e_2 / (2 D) - 1/4) t2
+// with e_k = alpha_k / d_k up to a common factor and D = e_0 + 6 e_1 + 3 e_2.
+// The weights are formed relative to the smallest s_k (index m), so that no
+// intermediate leaves float's range: with rho_k = s_m / s_k (rho_m = 1),
+//   JS: alpha_k / d_k = 1 / s_k^2 = rho_k^2 / s_m^2, the common factor dropped;
+//   Z:  alpha_k / d_k = 1 + (tau / s_k)^2 = 1 + (R rho_k)^2 with R = tau / s_m,
+//       and, where R > 1e18, R^2 rho_k^2 (the 1 is below 1e-36 of the rest).
+// Where eps / 3 is below float's range (WENO-Z) an indicator of a stencil
+// without variation is 0; then rho_k = 0 for the others (their weights
+// vanish against it, as in double), rho_k = 1 between equal indicators, and
+// R = 0 where tau = 0.
+template <int VAR>
+__device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
+    const dw x0 = dw_sub(a, b), y0 = dw_sub(b, c), z0 = dw_sub(c, d);
+    const dw x1 = dw_sub(x0, dw{2.0f * b.hi, 2.0f * b.lo});     // a - 3b
+    const dw y1 = dw_add(b, c);
+    const dw z1 = dw_add(z0, dw{2.0f * c.hi, 2.0f * c.lo});     // 3c - d
+    const dw k = {4.33333349f, -1.58945719e-07f};              // 13/3
+    const dw s0 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(x0, x0)), dw_mul(x1, x1)), eps3);
+    const dw s1 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(y0, y0)), dw_mul(y1, y1)), eps3);
+    const dw s2 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(z0, z0)), dw_mul(z1, z1)), eps3);
+    dw sm = s0;
+    if (s1.hi < sm.hi) sm = s1;
+    if (s2.hi < sm.hi) sm = s2;
+    const dw one = {1.0f, 0.0f};
+    const dw r0 = dw_eq(s0, sm) ? one : dw_div(sm, s0);
+    const dw r1 = dw_eq(s1, sm) ? one : dw_div(sm, s1);
+    const dw r2 = dw_eq(s2, sm) ? one : dw_div(sm, s2);
+    dw e0 = dw_mul(r0, r0), e1 = dw_mul(r1, r1), e2 = dw_mul(r2, r2);
+    if constexpr (VAR == 1) {
+        dw tau = dw_sub(s0, s2);
+        if (tau.hi < 0.0f) tau = dw_neg(tau);
+        const dw R = tau.hi == 0.0f ? dw{0.0f, 0.0f} : dw_div(tau, sm);
+        if (R.hi <= 1.0e18f) {
+            const dw R2 = dw_mul(R, R);
+            e0 = dw_add_same(one, dw_mul(R2, e0));
+            e1 = dw_add_same(one, dw_mul(R2, e1));
+            e2 = dw_add_same(one, dw_mul(R2, e2));
+        }
+    }
+    const dw D = dw_add_same(dw_add_same(e0, dw_mul_f(e1, 6.0f)), dw_mul_f(e2, 3.0f));
+    const dw inv = dw_div(one, D);
+    const dw w0 = dw_mul(e0, inv);
+    const dw w2 = dw_add(dw_mul_f(dw_mul(e2, inv), 1.5f), dw{-0.25f, 0.0f});
+    return dw_add(dw_mul(w0, dw_sub(x0, y0)), dw_mul(w2, dw_sub(y0, z0)));
+}
+
 // Eq. (FWENO) for one characteristic field from its 11 projections:
 // P[0] = L.central, P[1..5] = L.dF at i-3/2 .. i+5/2, P[6..10] = L.du there.
 //
@@ -371,13 +521,31 @@ __device__ __forceinline__ void phi_nd(double a, double b, double c, double d, d
 // for both weight variants: the factor 1/2 is applied once to the result.
 // With the IS_k / 3 form above the epsilon passed in is eps43 = 4 eps / 3,
 // and F = P[0] + (phi_N^- - phi_N^+)/2 = P[0] + (Nm/Dm - Np/Dp)/6.
-template <typename Real, int VAR>
+template <typename Real, int VAR, bool DWW = false>
 __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps43) {
     Real p[5], q[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         p[j] = P[1 + j] + alpha * P[6 + j];
         q[j] = P[1 + j] - alpha * P[6 + j];
+    }
+    if constexpr (std::is_same<Real, double>::value && DWW) {
+        dw Pd[11];
+#pragma unroll
+        for (int j = 1; j < 11; ++j) Pd[j] = dw_from_double(P[j]);
+        const dw ad = dw_from_double(alpha);
+        dw pd[5], qd[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const dw am = dw_mul(ad, Pd[6 + j]);
+            pd[j] = dw_add(Pd[1 + j], am);
+            qd[j] = dw_sub(Pd[1 + j], am);
+        }
+        const dw e3 = dw_from_double(eps43);
+        const dw Np = phi_dw<VAR>(pd[0], pd[1], pd[2], pd[3], e3);
+        const dw Nm = phi_dw<VAR>(qd[4], qd[3], qd[2], qd[1], e3);
+        const dw r = dw_sub(Nm, Np);
+        return fma(1.0 / 6.0, dw_f2d(r.hi), fma(1.0 / 6.0, dw_f2d(r.lo), P[0]));
     }
     if constexpr (std::is_same<Real, double>::value) {
         double Np, Dp, Nm, Dm;
@@ -453,7 +621,7 @@ __device__ __forceinline__ void split_pair_f(float Pc0, const float2 (&Pc2)[5], 
 // six cells at sm + k*st (k = 0..5); quantities are `ncell` elements apart.
 // Ff receives the frame flux (rho, m_n, m_t1, m_t2, B_t1, B_t2, E) and
 // s1, s2 the CT transport fluxes F_{B_t} + <B_n v_t> of Eqs. (fct1)-(fct6).
-template <typename Real, int VAR, bool DIFF = false>
+template <typename Real, int VAR, bool DIFF = false, bool DWW = false>
 __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell, int st, const Phys<Real> &K,
                                           Real (&Ff)[7], Real &s1, Real &s2) {
     using m = M<Real>;
@@ -649,8 +817,8 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
                 Pl[x] = pc - ps;
             }
         }
-        Fu = weno_field<Real, VAR>(Pu, alu, eps);
-        Fl = weno_field<Real, VAR>(Pl, all, eps);
+        Fu = weno_field<Real, VAR, DWW>(Pu, alu, eps);
+        Fl = weno_field<Real, VAR, DWW>(Pl, all, eps);
     };
 
     // ---- fast pair: m = 1 (v - c_f, upper sign) and m = 7 (v + c_f)
@@ -697,8 +865,8 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
                 Pl[x] = pc - ps;
             }
         }
-        const Real Fu = weno_field<Real, VAR>(Pu, al_am, eps);
-        const Real Fl = weno_field<Real, VAR>(Pl, al_ap, eps);
+        const Real Fu = weno_field<Real, VAR, DWW>(Pu, al_am, eps);
+        const Real Fl = weno_field<Real, VAR, DWW>(Pl, al_ap, eps);
         sa = Fu + Fl;
         da = Fu - Fl;
     }
@@ -716,7 +884,7 @@ __device__ __forceinline__ void face_flux(const Real *__restrict__ sm, int ncell
 #pragma unroll
             for (int x = 0; x < 11; ++x) Pe[x] = X[x][0] - tau * gX[x];
         }
-        Fe = weno_field<Real, VAR>(Pe, al_e, eps);
+        Fe = weno_field<Real, VAR, DWW>(Pe, al_e, eps);
     }
     // ---- back-projection: F = sum over fields of (WENO flux) x (right
     // eigenvector).  The right eigenvectors of the fast pair (Rc +- Rs),

@@ -35,6 +35,7 @@ W5CT_WENO_JS = 0
 W5CT_WENO_Z = 1
 W5CT_FP64 = 0
 W5CT_FP32_BULK = 1
+W5CT_FP64_DW = 2
 
 EXPORTED = [
     "w5ct_config_default", "w5ct_create", "w5ct_destroy", "w5ct_set_stream", "w5ct_init_grid",

@@ -196,3 +196,48 @@ def test_phi_n_forms_equal_the_oracle(Z):
         worst32 = max(worst32, abs(kernel_phi_float(*v, eps, Z) - want) / scale)
     assert worst64 < 1e-13, worst64
     assert worst32 < 1e-13, worst32
+
+
+def kernel_phi_dw_form(a, b, c, d, eps, Z):
+    """phi_N as the double-word FP64 sweeps evaluate it (weno_field with the
+    double-word flag), in float64: the weights relative to the smallest
+    indicator s_m, rho_k = s_m / s_k, JS e_k = rho_k^2, WENO-Z e_k =
+    1 + (R rho_k)^2 with R = tau / s_m, or (R rho_k)^2 scaled by 1/R^2 where
+    R > 1e18.  An epsilon below float's normal range is 0 there."""
+    e3 = eps / 3.0
+    if e3 < 2.0 ** -126:
+        e3 = 0.0
+    k = 13.0 / 3.0
+    x0, y0, z0 = a - b, b - c, c - d
+    x1, y1, z1 = x0 - 2 * b, b + c, z0 + 2 * c
+    s = [k * x0 * x0 + x1 * x1 + e3, k * y0 * y0 + y1 * y1 + e3, k * z0 * z0 + z1 * z1 + e3]
+    sm = min(s)
+    rho = [1.0 if sk == sm else sm / sk for sk in s]
+    e = [r * r for r in rho]
+    if Z:
+        tau = abs(s[0] - s[2])
+        R = 0.0 if tau == 0.0 else (tau / sm if sm > 0 else np.inf)
+        if R <= 1e18:
+            e = [1.0 + R * R * ek for ek in e]
+    D = e[0] + 6 * e[1] + 3 * e[2]
+    return ((e[0] / D) * (x0 - y0) + (1.5 * e[2] / D - 0.25) * (y0 - z0)) / 3
+
+
+@pytest.mark.parametrize("Z", [0, 1])
+def test_phi_n_double_word_form_equals_the_oracle(Z):
+    """The ratio-to-the-smallest-indicator weights, on random stencils of
+    every scale and on stencils with flat parts (indicators at epsilon, or
+    0 where epsilon is below float's range), against the oracle's phi_N."""
+    rng = np.random.default_rng(31 + Z)
+    cfg = ora.make_config(weno_variant=Z)
+    eps = cfg.eps_z if Z else cfg.eps_js
+    cases = [rng.normal(0.0, 1.0, 4) * rng.choice([1e-6, 1e-3, 1.0, 1e3]) for _ in range(2000)]
+    cases += [np.array(v, dtype=float) for v in
+              ([1.0, 0, 0, 0], [0, 0, 0, 1.0], [0, 1.0, 0, 0], [0, 0, 1.0, 0], [1.0, 1.0, 0, 0], [2.0, 0, 0, -1.0],
+               [0, 0, 0, 0], [1e-3, 2e-3, 0, 0], [3.0, 1.0, 1.0, 3.0], [1.0, 1.0, 1.0, 1.0], [1e-20, 0, 0, 5.0])]
+    worst = 0.0
+    for v in cases:
+        want = ora.phi_n(*v, cfg)
+        got = kernel_phi_dw_form(*v, eps, Z)
+        worst = max(worst, abs(got - want) / max(np.abs(v).max(), 1e-300))
+    assert worst < 1e-13, worst

@@ -1,0 +1,121 @@
+"""W5CT_FP64_DW -- the FP64 path with the WENO part of every characteristic
+field's flux (LF split, smoothness indicators, nonlinear weights and
+interpolants of Sec. 2.2) in double-word arithmetic on the FP32 pipe -- held
+to the FP64 bar: one step equals the oracle to 1e-12 of the state scale on
+grids large enough for the default sweep tiles (the only tiles that take
+the double-word form), several steps stay within 1e-12 of the IEEE FP64
+path, and on small grids (short FP64 tiles) the mode is the FP64 path bit
+for bit."""
+import numpy as np
+import pytest
+
+from test_gpu_parity import TOL64, compare, make_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1812_04278_gb300 import build
+    build.build()
+    from paper_1812_04278_gb300 import inputs, w5ct
+    oracle.build()
+    return dict(torch=torch, O=oracle, I=inputs, W=w5ct)
+
+
+def solver(env, shape, precision, variant=1):
+    W, torch = env["W"], env["torch"]
+    dx = tuple(1.0 / n for n in shape)
+    return W.Solver(shape, dx, W.make_config(precision=precision, weno_variant=variant),
+                    stream=torch.cuda.current_stream().cuda_stream)
+
+
+# every sweep of these grids runs at least two default-tile blocks per SM,
+# so the double-word kernels run; (100, 70, 50) is ragged along every axis
+DEFAULT_TILE_SHAPES = [(100, 70, 50), (96, 64, 48)]
+
+
+@pytest.mark.parametrize("shape", DEFAULT_TILE_SHAPES)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp64_dw_one_step_matches_oracle(env, shape, variant):
+    I, W = env["I"], env["W"]
+    dx = tuple(1.0 / n for n in shape)
+    cons, bface = I.random_smooth_state(shape, seed=3 * sum(shape) + variant)
+    s, o = make_pair(env, shape, dx, cons, bface, precision=W.W5CT_FP64_DW, variant=variant)
+    dt = o.cfl_dt()
+    s.step(dt)
+    o.step(dt)
+    rel_state, rel_field = compare(s.get_state(), o.get_state())
+    assert rel_state.max() <= TOL64, rel_state
+    assert rel_field.max() <= 10 * TOL64, rel_field
+    # the double-word kernels ran: the state is not the IEEE FP64 one bit for bit
+    s64 = solver(env, shape, W.W5CT_FP64, variant)
+    s64.set_state(env["torch"].from_numpy(cons).cuda(), env["torch"].from_numpy(bface).cuda())
+    s64.step(dt)
+    a, b = s.get_state(), s64.get_state()
+    assert any(np.abs(x - y).max() > 0 for x, y in zip(a[:2], b[:2]))
+    s.close()
+    s64.close()
+
+
+def test_fp64_dw_turbulence_matches_oracle(env):
+    """One step of the turbulence workload's generator at 96^3 (the bench's
+    state family) against the oracle."""
+    I, W = env["I"], env["W"]
+    n = 96
+    shape = (n, n, n)
+    cons, bface = I.turbulent_state(n, seed=1812, seed_b=1813, mach=1.0, beta=1.0, dB_frac=0.1, kmin=2, kmax=32)
+    s, o = make_pair(env, shape, (1.0 / n,) * 3, cons, bface, precision=W.W5CT_FP64_DW)
+    dt = o.cfl_dt()
+    s.step(dt)
+    o.step(dt)
+    rel_state, _ = compare(s.get_state(), o.get_state())
+    assert rel_state.max() <= TOL64, rel_state
+    s.close()
+
+
+def test_fp64_dw_ten_steps_track_fp64(env):
+    """Ten fixed-dt steps of both FP64 forms from one turbulent state: the
+    double-word form stays within 1e-12 of the state scale of the IEEE one,
+    and div b stays at round-off."""
+    I, W, torch = env["I"], env["W"], env["torch"]
+    n = 96
+    shape = (n, n, n)
+    cons, bface = I.turbulent_state(n, seed=7, seed_b=8, mach=1.0, beta=1.0, dB_frac=0.1, kmin=2, kmax=32)
+    runs = []
+    dt = None
+    for prec in (W.W5CT_FP64, W.W5CT_FP64_DW):
+        s = solver(env, shape, prec)
+        s.set_state(torch.from_numpy(cons).cuda(), torch.from_numpy(bface).cuda())
+        if dt is None:
+            dt = 0.5 * s.cfl_dt()     # one dt for both, well inside the CFL limit
+        for _ in range(10):
+            s.step(dt)
+        runs.append((s.get_state(), s.div_b_norm()[0]))
+        s.close()
+    (a, _), (b, divb) = runs
+    S = max(np.abs(a[0]).max(), np.abs(a[1]).max())
+    dev = max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) / S
+    assert dev <= TOL64, dev
+    assert divb < 1e-12
+
+
+def test_fp64_dw_small_grid_is_the_fp64_path(env):
+    """On grids that take the short FP64 tiles the mode runs the IEEE kernels."""
+    I, W, torch = env["I"], env["W"], env["torch"]
+    shape = (20, 12, 16)
+    cons, bface = I.random_smooth_state(shape, seed=5)
+    out = []
+    for prec in (W.W5CT_FP64, W.W5CT_FP64_DW):
+        s = solver(env, shape, prec)
+        s.set_state(torch.from_numpy(cons).cuda(), torch.from_numpy(bface).cuda())
+        for _ in range(3):
+            s.step(0.01)
+        out.append(s.get_state())
+        s.close()
+    for x, y in zip(out[0][:2], out[1][:2]):
+        assert np.array_equal(x, y)
