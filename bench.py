@@ -198,7 +198,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "d0a6eb31f311821e", "fp64": 103.57, "fp32": 43.81, "fp64dw": 105.17}
+SWEEP_TRAFFIC = {"src": "b0cf470a7411ab8d", "fp64": 103.37, "fp32": 43.70, "fp64dw": 105.46}
 
 
 def hbm_gbs(traffic, launch_ms):
@@ -506,7 +506,7 @@ def run_native(args):
         },
         "fp64_dw": {
             "value": valuedw, "unit": "zone-updates/s", "ms_per_step": msdw / args.steps,
-            "dtype": "f64; WENO split, weights and interpolants in double-word f32 pairs (48-bit significand)",
+            "dtype": "f64; WENO indicators, weights and interpolants in double-word f32 pairs (48-bit significand)",
             "speedup_vs_fp64": valuedw / value64, "max_rel_vs_fp64": reldw, "error_steps": nlog,
             "div_b_linf": divbdw,
             "roofline": {"kernel": "sweep_kernel (FP64, double-word WENO)", "bound": "alu", "achieved": achdw,

@@ -62,14 +62,15 @@ extern "C" {
                                       into the face field and all reductions in
                                       double */
 #define W5CT_FP64_DW 2             /* W5CT_FP64 with the WENO part of each
-                                      characteristic field's flux (LF split,
-                                      smoothness indicators, nonlinear weights,
-                                      interpolants; Sec. 2.2) in double-word
-                                      arithmetic (pairs of floats, 48-bit
-                                      significand) on the FP32 pipe, in the
-                                      single-patch sweeps of the default tiles;
-                                      everything else, every stored value and
-                                      every other kernel as W5CT_FP64 */
+                                      characteristic field's flux (smoothness
+                                      indicators, nonlinear weights and the two
+                                      interpolants of the LF-split differences;
+                                      Sec. 2.2) in double-word arithmetic (pairs
+                                      of floats, 48-bit significand) on the FP32
+                                      pipe, in the single-patch sweeps of the
+                                      default tiles; everything else, every
+                                      stored value and every other kernel as
+                                      W5CT_FP64 */
 
 typedef struct w5ct_ctx w5ct_ctx;
 

@@ -390,20 +390,18 @@ __device__ __forceinline__ dw ef_twoprod(float a, float b) {
     const float p = __fmul_rn(a, b);
     return {p, __fmaf_rn(a, b, -p)};
 }
-// x + y for operands of any sign (relative error below 3 u^2)
+// x + y: TwoSum of the high parts, the low parts added to its error term,
+// Fast2Sum (the "sloppy" sum of Joldes et al.).  The error is about
+// 2 u^2 (|x| + |y|): relative to the result for operands of one sign, and
+// relative to the operands where they cancel -- the accuracy the WENO
+// differences need, whose double inputs enter with relative errors of
+// 2^-49 from the conversion anyway.
 __device__ __forceinline__ dw dw_add(dw x, dw y) {
-    const dw s = ef_twosum(x.hi, y.hi);
-    const dw t = ef_twosum(x.lo, y.lo);
-    const dw v = ef_fast2sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return ef_fast2sum(v.hi, __fadd_rn(t.lo, v.lo));
-}
-__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
-__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
-// x + y for operands of one sign (no cancellation; relative error ~ 2 u^2)
-__device__ __forceinline__ dw dw_add_same(dw x, dw y) {
     const dw s = ef_twosum(x.hi, y.hi);
     return ef_fast2sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
 // x * y with y a float, and with y a double-word
 __device__ __forceinline__ dw dw_mul_f(dw x, float y) {
     const dw c = ef_twoprod(x.hi, y);
@@ -484,9 +482,9 @@ __device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
     const dw y1 = dw_add(b, c);
     const dw z1 = dw_add(z0, dw{2.0f * c.hi, 2.0f * c.lo});     // 3c - d
     const dw k = {4.33333349f, -1.58945719e-07f};              // 13/3
-    const dw s0 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(x0, x0)), dw_mul(x1, x1)), eps3);
-    const dw s1 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(y0, y0)), dw_mul(y1, y1)), eps3);
-    const dw s2 = dw_add_same(dw_add_same(dw_mul(k, dw_mul(z0, z0)), dw_mul(z1, z1)), eps3);
+    const dw s0 = dw_add(dw_add(dw_mul(k, dw_mul(x0, x0)), dw_mul(x1, x1)), eps3);
+    const dw s1 = dw_add(dw_add(dw_mul(k, dw_mul(y0, y0)), dw_mul(y1, y1)), eps3);
+    const dw s2 = dw_add(dw_add(dw_mul(k, dw_mul(z0, z0)), dw_mul(z1, z1)), eps3);
     dw sm = s0;
     if (s1.hi < sm.hi) sm = s1;
     if (s2.hi < sm.hi) sm = s2;
@@ -501,12 +499,12 @@ __device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
         const dw R = tau.hi == 0.0f ? dw{0.0f, 0.0f} : dw_div(tau, sm);
         if (R.hi <= 1.0e18f) {
             const dw R2 = dw_mul(R, R);
-            e0 = dw_add_same(one, dw_mul(R2, e0));
-            e1 = dw_add_same(one, dw_mul(R2, e1));
-            e2 = dw_add_same(one, dw_mul(R2, e2));
+            e0 = dw_add(one, dw_mul(R2, e0));
+            e1 = dw_add(one, dw_mul(R2, e1));
+            e2 = dw_add(one, dw_mul(R2, e2));
         }
     }
-    const dw D = dw_add_same(dw_add_same(e0, dw_mul_f(e1, 6.0f)), dw_mul_f(e2, 3.0f));
+    const dw D = dw_add(dw_add(e0, dw_mul_f(e1, 6.0f)), dw_mul_f(e2, 3.0f));
     const dw inv = dw_div(one, D);
     const dw w0 = dw_mul(e0, inv);
     const dw w2 = dw_add(dw_mul_f(dw_mul(e2, inv), 1.5f), dw{-0.25f, 0.0f});
@@ -521,6 +519,10 @@ __device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
 // for both weight variants: the factor 1/2 is applied once to the result.
 // With the IS_k / 3 form above the epsilon passed in is eps43 = 4 eps / 3,
 // and F = P[0] + (phi_N^- - phi_N^+)/2 = P[0] + (Nm/Dm - Np/Dp)/6.
+//
+// DWW (double only): the split differences, formed in double, go to
+// double-word, phi_dw evaluates both interpolants there, and their
+// difference returns to double for the last FMAs with P[0].
 template <typename Real, int VAR, bool DWW = false>
 __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real eps43) {
     Real p[5], q[5];
@@ -530,16 +532,11 @@ __device__ __forceinline__ Real weno_field(const Real P[11], Real alpha, Real ep
         q[j] = P[1 + j] - alpha * P[6 + j];
     }
     if constexpr (std::is_same<Real, double>::value && DWW) {
-        dw Pd[11];
-#pragma unroll
-        for (int j = 1; j < 11; ++j) Pd[j] = dw_from_double(P[j]);
-        const dw ad = dw_from_double(alpha);
         dw pd[5], qd[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-            const dw am = dw_mul(ad, Pd[6 + j]);
-            pd[j] = dw_add(Pd[1 + j], am);
-            qd[j] = dw_sub(Pd[1 + j], am);
+            pd[j] = dw_from_double(p[j]);
+            qd[j] = dw_from_double(q[j]);
         }
         const dw e3 = dw_from_double(eps43);
         const dw Np = phi_dw<VAR>(pd[0], pd[1], pd[2], pd[3], e3);

@@ -1,10 +1,10 @@
 // w5ct_sweep64dw.cu -- the FP64 single-patch sweep kernels of the default
 // tiles with the WENO part of every characteristic field's flux in
-// double-word arithmetic (w5ct_physics.cuh, weno_field): the LF split of the
-// projected differences, the smoothness indicators, the nonlinear weights and
-// the two interpolants run on the FP32 pipe, while the cell box, the
-// eigenvectors, the projections, the back-projection and every stored value
-// stay in IEEE double.  A translation unit of its own so that it compiles in
+// double-word arithmetic (w5ct_physics.cuh, weno_field): the smoothness
+// indicators, the nonlinear weights and the two interpolants of the LF-split
+// differences run on the FP32 pipe, while the cell box, the eigenvectors,
+// the projections, the split itself, the back-projection and every stored
+// value stay in IEEE double.  A translation unit of its own so that it compiles in
 // parallel with the other sweeps.
 #include "w5ct_internal.h"
 

@@ -1,6 +1,6 @@
 """W5CT_FP64_DW -- the FP64 path with the WENO part of every characteristic
-field's flux (LF split, smoothness indicators, nonlinear weights and
-interpolants of Sec. 2.2) in double-word arithmetic on the FP32 pipe -- held
+field's flux (smoothness indicators, nonlinear weights and interpolants of
+Sec. 2.2) in double-word arithmetic on the FP32 pipe -- held
 to the FP64 bar: one step equals the oracle to 1e-12 of the state scale on
 grids large enough for the default sweep tiles (the only tiles that take
 the double-word form), several steps stay within 1e-12 of the IEEE FP64
