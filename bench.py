@@ -198,7 +198,7 @@ def kernel_source_hash():
 # at 128^3 (dram__bytes_read.sum + dram__bytes_write.sum / 128^3), valid for
 # the sweep source with the given hash; scaled to a launch by the zone count
 # (traffic grows with the zones: one tile pass per zone).
-SWEEP_TRAFFIC = {"src": "b0cf470a7411ab8d", "fp64": 103.37, "fp32": 43.70, "fp64dw": 105.46}
+SWEEP_TRAFFIC = {"src": "94dd87415640b72f", "fp64": 103.51, "fp32": 43.84, "fp64dw": 105.32}
 
 
 def hbm_gbs(traffic, launch_ms):

@@ -474,7 +474,10 @@ __device__ __forceinline__ double dw_f2d(float f) {
 // Where eps / 3 is below float's range (WENO-Z) an indicator of a stencil
 // without variation is 0; then rho_k = 0 for the others (their weights
 // vanish against it, as in double), rho_k = 1 between equal indicators, and
-// R = 0 where tau = 0.
+// R = 0 where tau = 0.  An indicator below float's normal range (stencil
+// differences under about 1e-19) counts as 0 as well: the reciprocal of a
+// subnormal is not representable, and in double the weights of such
+// stencils are set by rounding noise anyway.
 template <int VAR>
 __device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
     const dw x0 = dw_sub(a, b), y0 = dw_sub(b, c), z0 = dw_sub(c, d);
@@ -482,9 +485,10 @@ __device__ __forceinline__ dw phi_dw(dw a, dw b, dw c, dw d, dw eps3) {
     const dw y1 = dw_add(b, c);
     const dw z1 = dw_add(z0, dw{2.0f * c.hi, 2.0f * c.lo});     // 3c - d
     const dw k = {4.33333349f, -1.58945719e-07f};              // 13/3
-    const dw s0 = dw_add(dw_add(dw_mul(k, dw_mul(x0, x0)), dw_mul(x1, x1)), eps3);
-    const dw s1 = dw_add(dw_add(dw_mul(k, dw_mul(y0, y0)), dw_mul(y1, y1)), eps3);
-    const dw s2 = dw_add(dw_add(dw_mul(k, dw_mul(z0, z0)), dw_mul(z1, z1)), eps3);
+    auto normal_or_zero = [](dw s) { return s.hi < 1.17549435e-38f ? dw{0.0f, 0.0f} : s; };
+    const dw s0 = normal_or_zero(dw_add(dw_add(dw_mul(k, dw_mul(x0, x0)), dw_mul(x1, x1)), eps3));
+    const dw s1 = normal_or_zero(dw_add(dw_add(dw_mul(k, dw_mul(y0, y0)), dw_mul(y1, y1)), eps3));
+    const dw s2 = normal_or_zero(dw_add(dw_add(dw_mul(k, dw_mul(z0, z0)), dw_mul(z1, z1)), eps3));
     dw sm = s0;
     if (s1.hi < sm.hi) sm = s1;
     if (s2.hi < sm.hi) sm = s2;

@@ -119,3 +119,30 @@ def test_fp64_dw_small_grid_is_the_fp64_path(env):
         s.close()
     for x, y in zip(out[0][:2], out[1][:2]):
         assert np.array_equal(x, y)
+
+
+def test_fp64_dw_near_flat_region_matches_oracle(env):
+    """Half of the box has momenta of 1e-21 (smoothness indicators below
+    float's normal range, which the double-word weights count as flat), the
+    other half an O(0.1) velocity wave, with jumps between them: every value
+    finite and one step equal to the oracle's to 1e-12 of the state scale."""
+    I, W = env["I"], env["W"]
+    shape = (96, 64, 48)
+    X, Y, Z, _ = I.cell_centres(shape)
+    rng = np.random.default_rng(44)
+    tiny = 1e-21 * rng.normal(size=(3,) + X.shape)
+    wave = 0.1 * np.stack([np.sin(4 * np.pi * X), np.cos(4 * np.pi * Y), np.sin(4 * np.pi * Z)])
+    v = np.where(X < 0.5, tiny, wave)
+    bface = np.stack([np.full_like(X, 1.0), np.full_like(X, 0.5), np.full_like(X, 0.2)])
+    cons, bface = I.assemble(np.ones_like(X), v, np.ones_like(X), bface)
+    dx = tuple(1.0 / n for n in shape)
+    for variant in (0, 1):
+        s, o = make_pair(env, shape, dx, cons, bface, precision=W.W5CT_FP64_DW, variant=variant)
+        dt = o.cfl_dt()
+        s.step(dt)
+        o.step(dt)
+        got = s.get_state()
+        assert all(np.isfinite(x).all() for x in got[:2])
+        rel_state, _ = compare(got, o.get_state())
+        assert rel_state.max() <= TOL64, (variant, rel_state)
+        s.close()
