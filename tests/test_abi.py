@@ -55,6 +55,13 @@ def test_create_rejects_bad_config(w5, field, value):
     assert len(w5.w5ct_last_error(None)) > 0
 
 
+@pytest.mark.parametrize("precision", ["W5CT_FP64", "W5CT_FP32_BULK", "W5CT_FP64_DW"])
+def test_create_accepts_every_precision(w5, precision):
+    cfg = w5.w5ct_config_default()
+    cfg.precision = getattr(w5, precision)
+    w5.w5ct_destroy(w5.w5ct_create(cfg))
+
+
 def test_create_and_destroy_without_device_work(w5):
     ctx = w5.w5ct_create(w5.w5ct_config_default())
     with pytest.raises(w5.W5ctError) as e:
