@@ -69,7 +69,9 @@ extern "C" {
                                       of floats, 48-bit significand) on the FP32
                                       pipe, in the single-patch sweeps of the
                                       default tiles; everything else, every
-                                      stored value and every other kernel as
+                                      stored value and every other kernel
+                                      (grids too small for those tiles, the
+                                      batched, fused and adjoint paths) as
                                       W5CT_FP64 */
 
 typedef struct w5ct_ctx w5ct_ctx;
